@@ -1,0 +1,165 @@
+/*
+ * tm.h - exact delta-temporal motif counting on one GB300 (sm_103a).
+ *
+ * Computes, for a directed temporal multigraph and a window delta, the counts
+ * of all 36 two- and three-node, three-edge delta-temporal motifs of
+ * arXiv 2204.09236 (Problem 1, Sec. III; motif = Def. 2, instance = Def. 3),
+ * through the paper's counters Star[Type,d1,d2,d3] and Pair[d1,d2,d3]
+ * (Sec. IV-A) and Tri[Type,di,dj,dk] (Sec. IV-B).
+ *
+ * Conventions shared by every call:
+ *   - An edge is (src[i], dst[i], t[i]); its edge id is the index i.
+ *   - Edges are totally ordered by (t, edge id). Def. 2 only asks
+ *     t1 <= t2 <= t3; with this order every 3-edge set is counted at most once.
+ *     The window test is t3 - t1 <= delta on raw timestamps.
+ *   - Direction codes: o (outward from the centre) = 0, in = 1.
+ *     Types I/II/III = 0/1/2 (Sec. IV-A star types, Sec. IV-B triangle types).
+ *     Flat cell index: Star/Tri ((T*2+a)*2+b)*2+c, Pair (a*2+b)*2+c.
+ *   - The 56-cell raw layout is star[24] | pair[8] | tri[24].
+ *   - out[36] is row-major out[i][j] = count of M_(i+1)(j+1); tm_layout gives
+ *     the edge pattern of each entry.
+ *   - Every call returns TM_OK (0) or a negative TM_E* code, and records a
+ *     message that tm_last_error() returns (per host thread). Calls that
+ *     return a pointer return NULL on error.
+ *   - No call falls back to the CPU: without a CUDA device every counting
+ *     call fails with TM_ECUDA.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TM_OK = 0,
+    TM_EINVAL = -1,   /* invalid argument or input graph */
+    TM_ENOMEM = -2,   /* device allocation failed */
+    TM_ECUDA = -3,    /* CUDA runtime error (message names the call) */
+    TM_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    TM_EBUDGET = -5   /* request exceeds a memory budget */
+};
+
+/* Opaque graph resident in device memory; owns its buffers. */
+typedef struct tm_graph tm_graph;
+
+/*
+ * Builds the device-resident graph: sorts the edges by (t, edge id), builds
+ * every node's incident sequence S_u (Table 1; S_u of Alg. 1 and Alg. 2) and
+ * every node pair's edge list E_(v,w) (Alg. 2), with a hash from node pair to
+ * list.
+ *   src, dst: int32[m] node ids, >= 0, src[i] != dst[i]. n = max id + 1.
+ *   t:        int64[m] timestamps; max(t) - min(t) must fit in int64.
+ *   m:        number of edges, 0 <= m < 2^30. m == 0 builds an empty graph.
+ * The three pointers may be host or device memory (each is classified with
+ * cudaPointerGetAttributes); they are read during the call only and may be
+ * NULL when m == 0. Runs on the library's own stream and returns after the
+ * build has finished. Returns NULL on error (TM_EINVAL for a rejected input:
+ * m out of range, NULL pointer, negative id, self-loop, timestamp span
+ * overflow; TM_ENOMEM, TM_ECUDA otherwise).
+ */
+tm_graph *tm_build(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t m);
+
+/* Same as tm_build, enqueued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream). Device inputs must be ready in stream order. The call
+ * still waits for one small device-to-host read (node count, timestamp
+ * range, validation flags) before it sizes the graph's buffers. */
+tm_graph *tm_build_async(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t m,
+                         void *stream);
+
+/* Releases the graph's device memory after the library stream has drained.
+ * Work that other streams still have queued on the graph must be complete
+ * (synchronise them first). NULL-safe. */
+void tm_free(tm_graph *g);
+
+/* Releases the graph's device memory in stream order on `stream`: the
+ * buffers return to the pool once the work queued before this call on that
+ * stream has finished. The handle is invalid on return. NULL-safe. */
+void tm_free_async(tm_graph *g, void *stream);
+
+/*
+ * Counts all 36 motifs for window delta (>= 0; delta == 0 counts only triples
+ * that share one timestamp). out: host uint64[36], row-major 6x6 as above.
+ * Synchronous. The graph is not modified; concurrent calls on one graph from
+ * several host threads are allowed.
+ * Errors: TM_EINVAL (NULL graph/out, delta < 0), TM_ECUDA.
+ */
+int tm_count(const tm_graph *g, int64_t delta, uint64_t out[36]);
+
+/*
+ * The paper's own counters (Sec. IV-A, IV-B) for window delta: star[24] =
+ * Star[T][d1][d2][d3], pair[8] = Pair[d1][d2][d3], tri[24] =
+ * Tri[T][di][dj][dk], host memory. Synchronous.
+ */
+int tm_count_raw(const tm_graph *g, int64_t delta, uint64_t star[24], uint64_t pair[8],
+                 uint64_t tri[24]);
+
+/*
+ * Enqueues the count on `stream` and writes the 56 raw cells (star|pair|tri)
+ * to dev_cells, a device uint64[56] owned by the caller. Returns as soon as
+ * the work is enqueued; the cells are valid once the stream reaches that
+ * point. Must not overlap another count that uses the same dev_cells.
+ */
+int tm_count_async(const tm_graph *g, int64_t delta, void *stream, uint64_t *dev_cells);
+
+/*
+ * The 56 raw cells of the centres listed in `centres` only (host int32[k],
+ * each in [0, n)): their Star and Pair cells (Alg. 1 run at those centres)
+ * and their Tri type-II cells (the triangles whose opposite edge is in the
+ * middle of the time order, Sec. IV-B). Tri types I and III are left zero.
+ * Used to compare single centres against a reference at full graph size.
+ */
+int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, int32_t k,
+                     uint64_t cells[56]);
+
+/*
+ * Folds 56 raw cells into the 36 classes (out[36] as above) on the host.
+ * Returns the number of classes whose isomorphic cells disagree (the pair
+ * mirror cells, Sec. IV-A; the three triangle cells of a class, one per
+ * type, Sec. IV-B): 0 for any output of this library.
+ */
+int tm_merge(const uint64_t cells[56], uint64_t out[36]);
+
+/* Writes the edge pattern of each class, codes[i*6+j] = pattern of
+ * M_(i+1)(j+1): edges in time order, nodes 1,2,3 by first appearance, e.g.
+ * "12 13 21". Returns TM_OK. */
+int tm_layout(char codes[36][16]);
+
+/* Number of nodes / edges of a built graph (-1 for NULL). */
+int64_t tm_graph_nodes(const tm_graph *g);
+int64_t tm_graph_edges(const tm_graph *g);
+
+/* Kernels this library has launched in this process so far (all devices). */
+uint64_t tm_launch_count(void);
+
+/*
+ * Phase timers (tracing). While enabled, the library records a CUDA event
+ * pair on the launching stream around each phase below, so a phase's time is
+ * its device time on that stream. tm_profile_read waits for the recorded
+ * events, adds each phase's elapsed milliseconds into ms[TM_NPHASES] and its
+ * number of timed occurrences into calls[TM_NPHASES] (both host arrays,
+ * either may be NULL), and clears the record.
+ */
+enum {
+    TM_PH_VALIDATE = 0, /* input upload and validation */
+    TM_PH_TIME_SORT,    /* radix sort of the edges by (t, edge id) */
+    TM_PH_INCIDENT,     /* S_u for every centre */
+    TM_PH_PAIRS,        /* pair lists, pair hash, same-neighbour links */
+    TM_PH_STAR_PAIR,    /* the Star/Pair counting kernel */
+    TM_PH_TRI,          /* the Tri counting kernel */
+    TM_NPHASES
+};
+void tm_profile_enable(int on);
+int tm_profile_read(double ms[], uint64_t calls[]);
+
+/* Message of the last failed call on this host thread; *code (if not NULL)
+ * receives its TM_E* code. Never NULL. */
+const char *tm_last_error(int *code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TM_H */

@@ -1,0 +1,461 @@
+// tm_build: the device-resident graph.
+//
+// Steps (one stream):
+//   1. validate ids / self-loops, find n, min t, max t          (k_validate)
+//   2. stable radix sort of the edges by t - t_min -> rank order  (ties keep
+//      the edge-id order: the (t, edge id) total order)
+//   3. incident entries of every centre, stable radix sort by centre: S_u in
+//      (t, id) order for every u (Table 1; "get S_u" in Alg. 1 and Alg. 2)
+//   4. in-count prefix over the entries (cin), entry positions of each edge
+//   5. stable radix sort of the edges by node pair: every E_(v,w) (Alg. 2) is
+//      a run of the pair list in rank order; a hash maps a pair to its run
+//   6. links between consecutive same-neighbour entries of a centre
+#include <cstring>
+#include <vector>
+
+#include "tm_internal.cuh"
+
+namespace tmi {
+
+namespace {
+
+struct Validation {
+    int32_t max_id;
+    int32_t bad_neg;
+    int32_t bad_loop;
+    int32_t pad;
+    long long tmin;
+    long long tmax;
+};
+
+__global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                           const int64_t *__restrict__ t, int64_t m, Validation *v) {
+    int32_t mx = -1, neg = 0, loop = 0;
+    long long tmn = LLONG_MAX, tmx = LLONG_MIN;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = src[e], b = dst[e];
+        neg |= (a < 0) | (b < 0);
+        loop |= a == b;
+        mx = max(mx, max(a, b));
+        long long x = t[e];
+        tmn = min(tmn, x);
+        tmx = max(tmx, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        neg |= __shfl_xor_sync(0xffffffffu, neg, o);
+        loop |= __shfl_xor_sync(0xffffffffu, loop, o);
+        tmn = min(tmn, __shfl_xor_sync(0xffffffffu, tmn, o));
+        tmx = max(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&v->max_id, mx);
+        if (neg) atomicOr(&v->bad_neg, 1);
+        if (loop) atomicOr(&v->bad_loop, 1);
+        atomicMin(&v->tmin, tmn);
+        atomicMax(&v->tmax, tmx);
+    }
+}
+
+__global__ void k_validation_init(Validation *v) {
+    v->max_id = -1;
+    v->bad_neg = 0;
+    v->bad_loop = 0;
+    v->tmin = LLONG_MAX;
+    v->tmax = LLONG_MIN;
+}
+
+template <typename K>
+__global__ void k_time_keys(const int64_t *__restrict__ t, int64_t m, long long tmin,
+                            K *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (K)((unsigned long long)t[e] - (unsigned long long)tmin);
+        vals[e] = (uint32_t)e;
+    }
+}
+
+// Edges in rank order: rank i -> (src, dst, relative t).
+template <typename K>
+__global__ void k_rank_edges(const K *__restrict__ tkey, const uint32_t *__restrict__ perm,
+                             const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                             int64_t m, int32_t *__restrict__ esrc, int32_t *__restrict__ edst,
+                             int64_t *__restrict__ et, int32_t *__restrict__ deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = perm[i];
+        int32_t a = src[e], b = dst[e];
+        esrc[i] = a;
+        edst[i] = b;
+        et[i] = (int64_t)tkey[i];
+        atomicAdd(&deg[a], 1);
+        atomicAdd(&deg[b], 1);
+    }
+}
+
+// Incident entries in rank order, keyed by centre: entry 2i+side of edge rank i
+// is at its source (side 0, direction o) or destination (side 1, direction in).
+__global__ void k_entry_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
+                             int64_t m, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = j >> 1;
+        int side = (int)(j & 1);
+        keys[j] = (uint32_t)(side ? edst[i] : esrc[i]);
+        vals[j] = (uint32_t)j;  // (rank << 1) | side
+    }
+}
+
+__global__ void k_dir_flags(const uint32_t *__restrict__ code, int64_t n2, int32_t *__restrict__ f) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x)
+        f[p] = (int32_t)(code[p] & 1u);
+}
+
+__global__ void k_fill_T(const uint32_t *__restrict__ centre, const uint32_t *__restrict__ code,
+                         const int32_t *__restrict__ cin, const int32_t *__restrict__ esrc,
+                         const int32_t *__restrict__ edst, const int64_t *__restrict__ et,
+                         int64_t n2, TEnt *__restrict__ T, int32_t *__restrict__ pos_src,
+                         int32_t *__restrict__ pos_dst) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = code[p];
+        int32_t rank = (int32_t)(c >> 1);
+        int side = (int)(c & 1u);
+        TEnt e;
+        e.t = et[rank];
+        e.nbr = (uint32_t)(side ? esrc[rank] : edst[rank]) | ((uint32_t)side << 31);
+        e.rank = rank;
+        e.cin = cin[p];
+        e.prev = -1;
+        e.next = -1;
+        e.centre = (int32_t)centre[p];
+        T[p] = e;
+        if (side) pos_dst[rank] = (int32_t)p;
+        else pos_src[rank] = (int32_t)p;
+    }
+}
+
+template <typename K>
+__global__ void k_pair_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
+                            int64_t m, int nb, K *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t a = (uint32_t)esrc[i], b = (uint32_t)edst[i];
+        uint32_t lo = min(a, b), hi = max(a, b);
+        keys[i] = ((K)lo << nb) | (K)hi;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+template <typename K>
+__global__ void k_pair_flags(const K *__restrict__ pkey, const uint32_t *__restrict__ pl,
+                             const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
+                             int64_t m, int32_t *__restrict__ rank_out,
+                             int32_t *__restrict__ srcmin, int32_t *__restrict__ head) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t r = pl[k];
+        rank_out[k] = (int32_t)r;
+        srcmin[k] = esrc[r] < edst[r] ? 1 : 0;
+        head[k] = (k == 0 || pkey[k] != pkey[k - 1]) ? 1 : 0;
+    }
+}
+
+// Consecutive edges of one node pair are consecutive same-neighbour entries
+// at both of its nodes: link their entries.
+template <typename K>
+__global__ void k_links(const K *__restrict__ pkey, const int32_t *__restrict__ pl_rank,
+                        const int32_t *__restrict__ esrc, const int32_t *__restrict__ pos_src,
+                        const int32_t *__restrict__ pos_dst, int64_t m, TEnt *__restrict__ T) {
+    for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (pkey[k] != pkey[k - 1]) continue;
+        int32_t r = pl_rank[k], rp = pl_rank[k - 1];
+        // node `esrc[r]`: e_k sits at its source; e_{k-1} at whichever side is that node
+        int32_t c0 = esrc[r];
+        int32_t cur0 = pos_src[r], cur1 = pos_dst[r];
+        int32_t prv0 = esrc[rp] == c0 ? pos_src[rp] : pos_dst[rp];
+        int32_t prv1 = esrc[rp] == c0 ? pos_dst[rp] : pos_src[rp];
+        T[cur0].prev = prv0;
+        T[prv0].next = cur0;
+        T[cur1].prev = prv1;
+        T[prv1].next = cur1;
+    }
+}
+
+template <typename K>
+__global__ void k_run_begins(const K *__restrict__ pkey, const int32_t *__restrict__ head,
+                              const int32_t *__restrict__ run_id, const int32_t *__restrict__ pl_rank,
+                              const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
+                              int64_t m, int32_t *__restrict__ run_begin) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (head[k]) run_begin[run_id[k]] = (int32_t)k;
+    }
+}
+
+__global__ void k_hash_fill(const int32_t *__restrict__ run_begin, int64_t nruns, int64_t m,
+                            const int32_t *__restrict__ pl_rank, const int32_t *__restrict__ esrc,
+                            const int32_t *__restrict__ edst, PairSlot *__restrict__ H,
+                            uint32_t mask) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nruns;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = run_begin[j];
+        int32_t e = j + 1 < nruns ? run_begin[j + 1] : (int32_t)m;
+        int32_t r = pl_rank[b];
+        uint64_t key = pair_key((uint32_t)esrc[r], (uint32_t)edst[r]);
+        uint32_t h = hash_pair(key) & mask;
+        for (uint32_t probe = 0; probe <= mask; probe++) {
+            unsigned long long prev =
+                atomicCAS((unsigned long long *)&H[h].key, (unsigned long long)EMPTY_KEY,
+                          (unsigned long long)key);
+            if (prev == EMPTY_KEY) {
+                H[h].begin = b;
+                H[h].end = e;
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+}
+
+int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+unsigned grid_for(int64_t n, int threads = 256) {
+    int64_t blocks = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    return (unsigned)(blocks > 0 ? blocks : 1);
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename K>
+void build_pairs(DevGraph &g, const int32_t *esrc, const int32_t *edst, int nb, cudaStream_t s) {
+    const int64_t m = g.m;
+    K *pk = dev_alloc_n<K>(m, s), *pk2 = dev_alloc_n<K>(m, s);
+    uint32_t *pv = dev_alloc_n<uint32_t>(m, s), *pv2 = dev_alloc_n<uint32_t>(m, s);
+    TM_LAUNCH(k_pair_keys<K>, grid_for(m), 256, 0, s, esrc, edst, m, nb, pk, pv);
+    K *sk;
+    uint32_t *sv;
+    if constexpr (sizeof(K) == 4)
+        radix_sort_u32(pk, pv, pk2, pv2, m, 2 * nb, s, &sk, &sv);
+    else
+        radix_sort_u64(pk, pv, pk2, pv2, m, 2 * nb, s, &sk, &sv);
+
+    int32_t *srcmin = dev_alloc_n<int32_t>(m, s);
+    int32_t *head = dev_alloc_n<int32_t>(m, s);
+    int32_t *run_id = dev_alloc_n<int32_t>(m + 1, s);
+    TM_LAUNCH(k_pair_flags<K>, grid_for(m), 256, 0, s, sk, sv, esrc, edst, m, g.pl_rank, srcmin,
+              head);
+    exclusive_scan_i32(srcmin, g.pl_cum, m, s);
+    exclusive_scan_i32(head, run_id, m, s);
+    TM_LAUNCH(k_links<K>, grid_for(m), 256, 0, s, sk, g.pl_rank, esrc, g.pos_src, g.pos_dst, m,
+              g.T);
+    int32_t nruns = 0;
+    TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TM_CUDA(cudaStreamSynchronize(s));
+    uint64_t cap = 16;
+    while (cap < 2ull * (uint64_t)nruns) cap <<= 1;
+    g.hash = dev_alloc_n<PairSlot>((int64_t)cap, s);
+    g.hash_mask = (uint32_t)(cap - 1);
+    TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * cap, s));
+    int32_t *run_begin = dev_alloc_n<int32_t>(nruns + 1, s);
+    TM_LAUNCH(k_run_begins<K>, grid_for(m), 256, 0, s, sk, head, run_id, g.pl_rank, esrc, edst,
+              m, run_begin);
+    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, g.pl_rank,
+              esrc, edst, g.hash, g.hash_mask);
+    dev_free(run_begin, s);
+    dev_free(run_id, s);
+    dev_free(head, s);
+    dev_free(srcmin, s);
+    dev_free(pk, s);
+    dev_free(pk2, s);
+    dev_free(pv, s);
+    dev_free(pv2, s);
+}
+
+template <typename K>
+void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
+                  int keybits, int32_t *esrc, int32_t *edst, int64_t *et, int32_t *deg,
+                  cudaStream_t s) {
+    const int64_t m = g.m;
+    K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
+    uint32_t *v1 = dev_alloc_n<uint32_t>(m, s), *v2 = dev_alloc_n<uint32_t>(m, s);
+    TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, t, m, (long long)g.tmin, k1, v1);
+    K *sk;
+    uint32_t *sv;
+    if constexpr (sizeof(K) == 4)
+        radix_sort_u32(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+    else
+        radix_sort_u64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+    TM_LAUNCH(k_rank_edges<K>, grid_for(m), 256, 0, s, sk, sv, src, dst, m, esrc, edst, et, deg);
+    dev_free(k1, s);
+    dev_free(k2, s);
+    dev_free(v1, s);
+    dev_free(v2, s);
+}
+
+}  // namespace
+
+void free_graph(DevGraph &g, cudaStream_t s) {
+    dev_free(g.T, s);
+    dev_free(g.off, s);
+    dev_free(g.pos_src, s);
+    dev_free(g.pos_dst, s);
+    dev_free(g.pl_rank, s);
+    dev_free(g.pl_cum, s);
+    dev_free(g.hash, s);
+    g = DevGraph();
+}
+
+// Builds g from host or device arrays on stream s. Throws Error.
+void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_in, int64_t m,
+                 cudaStream_t s, DevGraph &g) {
+    if (m < 0 || m >= (int64_t(1) << 30)) fail(TM_EINVAL, "tm_build: m must be in [0, 2^30)");
+    if (m > 0 && (!src_in || !dst_in || !t_in))
+        fail(TM_EINVAL, "tm_build: NULL edge array with m > 0");
+    g = DevGraph();
+    g.m = m;
+    const int32_t *src = src_in, *dst = dst_in;
+    const int64_t *t = t_in;
+    int32_t *h_src = nullptr, *h_dst = nullptr;
+    int64_t *h_t = nullptr;
+    if (m > 0) {
+        // host arrays are copied in; device arrays are read in place
+        if (!is_device_ptr(src_in)) {
+            h_src = dev_alloc_n<int32_t>(m, s);
+            TM_CUDA(cudaMemcpyAsync(h_src, src_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+            src = h_src;
+        }
+        if (!is_device_ptr(dst_in)) {
+            h_dst = dev_alloc_n<int32_t>(m, s);
+            TM_CUDA(cudaMemcpyAsync(h_dst, dst_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+            dst = h_dst;
+        }
+        if (!is_device_ptr(t_in)) {
+            h_t = dev_alloc_n<int64_t>(m, s);
+            TM_CUDA(cudaMemcpyAsync(h_t, t_in, sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+            t = h_t;
+        }
+    }
+    auto release_inputs = [&]() {
+        if (h_src) dev_free(h_src, s);
+        if (h_dst) dev_free(h_dst, s);
+        if (h_t) dev_free(h_t, s);
+        h_src = h_dst = nullptr;
+        h_t = nullptr;
+    };
+
+    Validation hv;
+    {
+        PhaseTimer pt(TM_PH_VALIDATE, s);
+        Validation *dv = dev_alloc_n<Validation>(1, s);
+        TM_LAUNCH(k_validation_init, 1, 1, 0, s, dv);
+        if (m > 0) TM_LAUNCH(k_validate, grid_for(m), 256, 0, s, src, dst, t, m, dv);
+        TM_CUDA(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        TM_CUDA(cudaStreamSynchronize(s));
+        dev_free(dv, s);
+    }
+    if (hv.bad_neg || hv.bad_loop) {
+        release_inputs();
+        fail(TM_EINVAL, hv.bad_neg ? "tm_build: negative node id" : "tm_build: self-loop (src == dst)");
+    }
+    const int64_t n = (int64_t)hv.max_id + 1;
+    g.n = (int32_t)n;
+    uint64_t span = 0;
+    if (m > 0) {
+        span = (uint64_t)hv.tmax - (uint64_t)hv.tmin;
+        if (span > (uint64_t)INT64_MAX) {
+            release_inputs();
+            fail(TM_EINVAL, "tm_build: max(t) - min(t) does not fit in int64");
+        }
+        g.tmin = hv.tmin;
+    }
+
+    g.off = dev_alloc_n<int32_t>(n + 1, s);
+    g.T = dev_alloc_n<TEnt>(2 * m, s);
+    g.pos_src = dev_alloc_n<int32_t>(m, s);
+    g.pos_dst = dev_alloc_n<int32_t>(m, s);
+    g.pl_rank = dev_alloc_n<int32_t>(m, s);
+    g.pl_cum = dev_alloc_n<int32_t>(m + 1, s);
+    if (m == 0) {
+        TM_CUDA(cudaMemsetAsync(g.off, 0, sizeof(int32_t) * (n + 1), s));
+        TM_CUDA(cudaMemsetAsync(g.pl_cum, 0, sizeof(int32_t), s));
+        g.hash = dev_alloc_n<PairSlot>(16, s);
+        g.hash_mask = 15;
+        TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * 16, s));
+        TM_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
+
+    // 2. rank order
+    int32_t *esrc = dev_alloc_n<int32_t>(m, s), *edst = dev_alloc_n<int32_t>(m, s);
+    int64_t *et = dev_alloc_n<int64_t>(m, s);
+    int32_t *deg = dev_alloc_n<int32_t>(n, s);
+    TM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, s));
+    const int keybits = bits_for(span);
+    {
+    PhaseTimer pt(TM_PH_TIME_SORT, s);
+    if (keybits <= 32)
+        sort_by_time<uint32_t>(src, dst, t, g, keybits, esrc, edst, et, deg, s);
+    else
+        sort_by_time<uint64_t>(src, dst, t, g, keybits, esrc, edst, et, deg, s);
+    release_inputs();
+    exclusive_scan_i32(deg, g.off, n, s);
+    dev_free(deg, s);
+    }
+
+    // 3-4. S_u for every centre
+    {
+        PhaseTimer pt(TM_PH_INCIDENT, s);
+        const int64_t n2 = 2 * m;
+        uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
+        uint32_t *v1 = dev_alloc_n<uint32_t>(n2, s), *v2 = dev_alloc_n<uint32_t>(n2, s);
+        TM_LAUNCH(k_entry_keys, grid_for(n2), 256, 0, s, esrc, edst, m, k1, v1);
+        uint32_t *sk, *sv;
+        radix_sort_u32(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
+        int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
+        TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
+        exclusive_scan_i32(flags, cin, n2, s);
+        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, esrc, edst, et, n2, g.T,
+                  g.pos_src, g.pos_dst);
+        dev_free(flags, s);
+        dev_free(cin, s);
+        dev_free(k1, s);
+        dev_free(k2, s);
+        dev_free(v1, s);
+        dev_free(v2, s);
+    }
+    dev_free(et, s);
+
+    // 5-6. pair list, hash, same-neighbour links
+    const int nb = bits_for((uint64_t)(n - 1));
+    {
+        PhaseTimer pt(TM_PH_PAIRS, s);
+        if (2 * nb <= 32)
+            build_pairs<uint32_t>(g, esrc, edst, nb, s);
+        else
+            build_pairs<uint64_t>(g, esrc, edst, nb, s);
+    }
+    dev_free(esrc, s);
+    dev_free(edst, s);
+    TM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace tmi

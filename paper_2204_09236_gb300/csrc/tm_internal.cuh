@@ -1,0 +1,145 @@
+// Internal declarations of the GB300 temporal-motif library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "tm.h"
+
+namespace tmi {
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+[[noreturn]] void cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define TM_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) ::tmi::cuda_fail(e_, #call, __FILE__, __LINE__);       \
+    } while (0)
+
+// Every kernel launch of the library goes through TM_LAUNCH so that launch
+// errors are caught at the call site and launches are counted.
+extern std::atomic<uint64_t> g_launches;
+#define TM_LAUNCH(kernel, grid, block, smem, stream, ...)                              \
+    do {                                                                               \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                    \
+        ::tmi::g_launches.fetch_add(1, std::memory_order_relaxed);                     \
+        TM_CUDA(cudaGetLastError());                                                   \
+    } while (0)
+
+// Phase timer: records a CUDA event pair around a scope on stream s while
+// profiling is enabled (tm_profile_enable).
+struct PhaseTimer {
+    PhaseTimer(int phase, cudaStream_t s);
+    ~PhaseTimer();
+    int phase;
+    cudaStream_t stream;
+    cudaEvent_t start = nullptr;
+};
+
+// ------------------------------------------------------------- memory
+
+// Stream-ordered device allocation from the device's default memory pool
+// (its release threshold is raised once per device so freed blocks stay
+// cached for the next build).
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+template <typename T>
+T *dev_alloc_n(int64_t n, cudaStream_t s) {
+    return static_cast<T *>(dev_alloc(sizeof(T) * (size_t)(n > 0 ? n : 1), s));
+}
+
+int num_sms();
+
+// ------------------------------------------------------------ graph
+
+// One entry of a centre's time-sorted incident sequence S_u (Table 1 of the
+// paper: e = (t, v, dir) w.r.t. centre u), 32 bytes.
+struct TEnt {
+    int64_t t;       // timestamp minus the graph's smallest timestamp
+    uint32_t nbr;    // other endpoint v | dir << 31 (dir: 0 = o, 1 = in)
+    int32_t rank;    // position of the edge in the global (t, edge id) order
+    int32_t cin;     // inward entries before this one in the whole array
+    int32_t prev;    // previous entry of this centre with the same neighbour, or -1
+    int32_t next;    // next such entry, or -1
+    int32_t centre;  // u
+};
+static_assert(sizeof(TEnt) == 32, "TEnt must be 32 bytes");
+
+// Hash slot: unordered node pair -> its edge list E_(v,w) in the pair list.
+struct PairSlot {
+    uint64_t key;  // (smaller id) << 32 | larger id; EMPTY_KEY if unused
+    int32_t begin;
+    int32_t end;
+};
+constexpr uint64_t EMPTY_KEY = ~0ull;
+
+struct DevGraph {
+    int64_t m = 0;
+    int32_t n = 0;
+    int64_t tmin = 0;
+    TEnt *T = nullptr;          // 2m entries, grouped by centre, (t, id) order inside
+    int32_t *off = nullptr;     // n+1: S_u = T[off[u], off[u+1])
+    int32_t *pos_src = nullptr; // m, by rank: T position of the edge at its source
+    int32_t *pos_dst = nullptr; // m, by rank: T position at its destination
+    int32_t *pl_rank = nullptr; // m: pair list, grouped by node pair, ranks ascending
+    int32_t *pl_cum = nullptr;  // m+1: exclusive prefix of (src is the smaller id)
+    PairSlot *hash = nullptr;   // open addressing, linear probing
+    uint32_t hash_mask = 0;
+};
+
+__host__ __device__ inline uint64_t pair_key(uint32_t a, uint32_t b) {
+    return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
+}
+
+__host__ __device__ inline uint32_t hash_pair(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+// ------------------------------------------------------- primitives
+
+// Exclusive prefix sum: out[i] = sum(in[0..i)), out[n] = total. out may alias in
+// only if it is a different array; n >= 0.
+void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+// Sorts `keys`/`vals` of length n using the given scratch buffers of the same
+// length; on return the sorted data is in (*keys_out, *vals_out), which is
+// either the input or the scratch pair.
+void radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp,
+                    int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
+                    uint32_t **vals_out);
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
+                    int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
+                    uint32_t **vals_out);
+
+// --------------------------------------------------------- counting
+
+// Number of 56 raw cells: Star[24] | Pair[8] | Tri[24].
+constexpr int NCELLS = 56;
+
+// Adds the counts of entries [begin, end) of g.T (as e3 for Star/Pair and as
+// e_j for Tri type II) into dev_cells (uint64[56], device). When
+// `tri_types_all` is set the Tri type-I/III cells are filled from type II by
+// the triangle rotation identity after the whole graph has been counted.
+void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
+                  unsigned long long *dev_cells, cudaStream_t s);
+void launch_fill_tri_types(unsigned long long *dev_cells, cudaStream_t s);
+
+}  // namespace tmi

@@ -1,0 +1,238 @@
+"""Python binding of libtm.so (include/tm.h): argument marshalling only.
+
+Every step of the counting path runs in the library's CUDA kernels. The
+binding converts numpy arrays (host memory) or torch tensors (host or CUDA
+memory) to raw pointers, passes torch's current CUDA stream where a call takes
+a stream, and raises TmError for a negative status. There is no CPU fallback:
+if libtm.so has not been built, importing this module raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libtm.so"
+
+TM_OK, TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_ETIMEOUT, TM_EBUDGET = 0, -1, -2, -3, -4, -5
+
+if not _LIB_PATH.exists():
+    raise ImportError(f"{_LIB_PATH} is missing: build the CUDA library first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(str(_LIB_PATH))
+_P = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_lib.tm_build.restype = _P
+_lib.tm_build.argtypes = [_P, _P, _P, _i64]
+_lib.tm_build_async.restype = _P
+_lib.tm_build_async.argtypes = [_P, _P, _P, _i64, _P]
+_lib.tm_free.argtypes = [_P]
+_lib.tm_free_async.argtypes = [_P, _P]
+_lib.tm_count.argtypes = [_P, _i64, _P]
+_lib.tm_count_raw.argtypes = [_P, _i64, _P, _P, _P]
+_lib.tm_count_async.argtypes = [_P, _i64, _P, _P]
+_lib.tm_count_centres.argtypes = [_P, _i64, _P, ctypes.c_int32, _P]
+_lib.tm_merge.argtypes = [_P, _P]
+_lib.tm_layout.argtypes = [_P]
+_lib.tm_graph_nodes.restype = _i64
+_lib.tm_graph_nodes.argtypes = [_P]
+_lib.tm_graph_edges.restype = _i64
+_lib.tm_graph_edges.argtypes = [_P]
+_lib.tm_launch_count.restype = ctypes.c_uint64
+_lib.tm_profile_enable.argtypes = [ctypes.c_int]
+_lib.tm_profile_read.argtypes = [_P, _P]
+_lib.tm_last_error.restype = ctypes.c_char_p
+_lib.tm_last_error.argtypes = [ctypes.POINTER(ctypes.c_int)]
+
+LIBRARY_PATH = str(_LIB_PATH)
+
+
+class TmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def last_error():
+    c = ctypes.c_int(0)
+    msg = _lib.tm_last_error(ctypes.byref(c)).decode()
+    return c.value, msg
+
+
+def _check(rc):
+    if rc < 0:
+        code, msg = last_error()
+        raise TmError(rc, msg)
+    return rc
+
+
+def _ptr(x, dtype):
+    """Pointer of a contiguous array/tensor of `dtype`; returns (ptr, keepalive)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.uint64}[dtype]
+            if x.dtype != tdt:
+                raise TypeError(f"expected {tdt}, got {x.dtype}")
+            x = x.contiguous()
+            return ctypes.c_void_p(x.data_ptr() if x.numel() else None), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return (a.ctypes.data_as(ctypes.c_void_p) if a.size else ctypes.c_void_p(None)), a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Graph:
+    """A graph resident on the current CUDA device (tm_build)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self):
+        return int(_lib.tm_graph_nodes(self._h))
+
+    @property
+    def m(self):
+        return int(_lib.tm_graph_edges(self._h))
+
+    def free(self):
+        if self._h:
+            _lib.tm_free(self._h)
+            self._h = None
+
+    def free_async(self, stream=None):
+        if self._h:
+            _lib.tm_free_async(self._h, _stream_handle(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tm_build(src, dst, t):
+    """tm_build: src, dst int32[m], t int64[m] (numpy or torch, host or CUDA)."""
+    ps, ks = _ptr(src, np.int32)
+    pd, kd = _ptr(dst, np.int32)
+    pt, kt = _ptr(t, np.int64)
+    m = len(ks)
+    if not (len(kd) == m and len(kt) == m):
+        raise ValueError("src, dst and t must have the same length")
+    h = _lib.tm_build(ps, pd, pt, m)
+    if not h:
+        code, msg = last_error()
+        raise TmError(code, msg)
+    return Graph(h)
+
+
+def tm_build_async(src, dst, t, stream=None):
+    ps, ks = _ptr(src, np.int32)
+    pd, kd = _ptr(dst, np.int32)
+    pt, kt = _ptr(t, np.int64)
+    h = _lib.tm_build_async(ps, pd, pt, len(ks), _stream_handle(stream))
+    if not h:
+        code, msg = last_error()
+        raise TmError(code, msg)
+    return Graph(h)
+
+
+def tm_count(g, delta):
+    """36 class counts as a (6, 6) uint64 array, out[i, j] = M_(i+1)(j+1)."""
+    out = np.zeros(36, np.uint64)
+    _check(_lib.tm_count(g.handle, int(delta), out.ctypes.data_as(_P)))
+    return out.reshape(6, 6)
+
+
+def tm_count_raw(g, delta):
+    """The paper's counters: star[3,2,2,2], pair[2,2,2], tri[3,2,2,2]."""
+    s = np.zeros(24, np.uint64)
+    p = np.zeros(8, np.uint64)
+    q = np.zeros(24, np.uint64)
+    _check(_lib.tm_count_raw(g.handle, int(delta), s.ctypes.data_as(_P), p.ctypes.data_as(_P),
+                             q.ctypes.data_as(_P)))
+    return s.reshape(3, 2, 2, 2), p.reshape(2, 2, 2), q.reshape(3, 2, 2, 2)
+
+
+def tm_count_async(g, delta, dev_cells, stream=None):
+    """Enqueue the count; dev_cells is a CUDA uint64 tensor of 56 elements."""
+    pc, keep = _ptr(dev_cells, np.uint64)
+    _check(_lib.tm_count_async(g.handle, int(delta), _stream_handle(stream), pc))
+    return keep
+
+
+def tm_count_centres(g, delta, centres):
+    c = np.ascontiguousarray(centres, np.int32)
+    cells = np.zeros(56, np.uint64)
+    _check(_lib.tm_count_centres(g.handle, int(delta), c.ctypes.data_as(_P), len(c),
+                                 cells.ctypes.data_as(_P)))
+    return split_cells(cells)
+
+
+def split_cells(cells):
+    cells = np.asarray(cells, np.uint64).reshape(56)
+    return cells[:24].reshape(3, 2, 2, 2), cells[24:32].reshape(2, 2, 2), cells[32:].reshape(3, 2, 2, 2)
+
+
+def tm_merge(cells):
+    """56 raw cells -> ((6, 6) classes, number of inconsistent classes)."""
+    c = np.ascontiguousarray(cells, np.uint64).reshape(56)
+    out = np.zeros(36, np.uint64)
+    bad = _check(_lib.tm_merge(c.ctypes.data_as(_P), out.ctypes.data_as(_P)))
+    return out.reshape(6, 6), bad
+
+
+def tm_layout():
+    buf = ctypes.create_string_buffer(36 * 16)
+    _check(_lib.tm_layout(buf))
+    raw = buf.raw
+    return [[raw[16 * (6 * i + j):16 * (6 * i + j + 1)].split(b"\0")[0].decode()
+             for j in range(6)] for i in range(6)]
+
+
+def tm_launch_count():
+    return int(_lib.tm_launch_count())
+
+
+PHASES = ("validate", "time_sort", "incident", "pairs", "star_pair", "tri")
+
+
+def tm_profile_enable(on=True):
+    _lib.tm_profile_enable(1 if on else 0)
+
+
+def tm_profile_read():
+    """{phase: (device ms summed, timed occurrences)} since the last read."""
+    ms = np.zeros(len(PHASES), np.float64)
+    calls = np.zeros(len(PHASES), np.uint64)
+    _check(_lib.tm_profile_read(ms.ctypes.data_as(_P), calls.ctypes.data_as(_P)))
+    return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+
+
+# short aliases
+build = tm_build
+build_async = tm_build_async
+count = tm_count
+count_raw = tm_count_raw
+count_async = tm_count_async
+count_centres = tm_count_centres
+merge = tm_merge
+layout = tm_layout
+launch_count = tm_launch_count
