@@ -24,7 +24,11 @@
  *     ordered by (t, edge id), edge id = array index, and each 3-edge set is
  *     counted once, in that order. Every order comparison of Algorithm 2 is
  *     taken in this total order; delta tests use raw timestamps.
- *   - Window: t3 - t1 <= delta (Def. 2; Alg. 1 break test; Alg. 2).
+ *   - Window: t3 - t1 <= delta (Def. 2; Alg. 1 break test; Alg. 2). Every
+ *     window test is written as a difference of two timestamps compared with
+ *     delta (t_j - delta <= t_k is tested as t_j - t_k <= delta), so no sum
+ *     overflows; orc_build rejects graphs whose timestamp span does not fit
+ *     in int64, which keeps every difference representable.
  *   - dir_k of a triangle is relative to v = e_i.v (Sec. IV-B definition).
  *   - Self-loops are rejected (all workloads have u != v).
  */
@@ -110,15 +114,20 @@ void orc_free(orc_graph *g) {
     free(g);
 }
 
-/* Returns NULL on invalid input (negative id, self-loop, m < 0) or OOM. */
+/* Returns NULL on invalid input (negative id, self-loop, m < 0, timestamp
+ * span beyond int64) or OOM. */
 orc_graph *orc_build(int64_t m, const int32_t *src, const int32_t *dst, const int64_t *t) {
     if (m < 0) return NULL;
     int32_t n = 0;
+    int64_t tmin = 0, tmax = 0;
     for (int64_t e = 0; e < m; e++) {
         if (src[e] < 0 || dst[e] < 0 || src[e] == dst[e]) return NULL;
         if (src[e] + 1 > n) n = src[e] + 1;
         if (dst[e] + 1 > n) n = dst[e] + 1;
+        if (e == 0 || t[e] < tmin) tmin = t[e];
+        if (e == 0 || t[e] > tmax) tmax = t[e];
     }
+    if (m > 0 && (uint64_t)tmax - (uint64_t)tmin > (uint64_t)INT64_MAX) return NULL;
     orc_graph *g = calloc(1, sizeof(orc_graph));
     if (!g) return NULL;
     g->m = m;
@@ -262,7 +271,7 @@ static void alg2_first_edge(const orc_graph *g, int64_t i, int64_t se, int64_t d
     const s_entry ei = S[i];
     for (int64_t j = i + 1; j < se; j++) {
         const s_entry ej = S[j];
-        if (ej.t > ei.t + delta) break;
+        if (ej.t - ei.t > delta) break;
         if (ej.v == ei.v) continue;
         const int32_t v = ei.v, w = ej.v;
         int64_t b, e;
@@ -271,19 +280,19 @@ static void alg2_first_edge(const orc_graph *g, int64_t i, int64_t se, int64_t d
         int64_t l = b, r = e;
         while (l < r) {
             int64_t mid = (l + r) / 2;
-            if (g->P[mid].t < ej.t - delta) l = mid + 1;
+            if (ej.t - g->P[mid].t > delta) l = mid + 1;
             else r = mid;
         }
         for (int64_t k = l; k < e; k++) {
             const p_entry ek = g->P[k];
             const int dk = ek.src == v ? O : IN; /* o: from v to w */
-            if (ek.t >= ej.t - delta && before(ek.t, ek.id, ei.t, ei.id)) {
+            if (ej.t - ek.t <= delta && before(ek.t, ek.id, ei.t, ei.id)) {
                 TRI(T_I, ei.dir, ej.dir, dk)++;
             } else if (before(ei.t, ei.id, ek.t, ek.id) && before(ek.t, ek.id, ej.t, ej.id)) {
                 TRI(T_II, ei.dir, ej.dir, dk)++;
-            } else if (before(ej.t, ej.id, ek.t, ek.id) && ek.t <= ei.t + delta) {
+            } else if (before(ej.t, ej.id, ek.t, ek.id) && ek.t - ei.t <= delta) {
                 TRI(T_III, ei.dir, ej.dir, dk)++;
-            } else if (ek.t > ei.t + delta) {
+            } else if (ek.t - ei.t > delta) {
                 break;
             }
         }

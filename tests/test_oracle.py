@@ -360,6 +360,18 @@ def test_rejects_bad_input():
         G.count(-1)
 
 
+def test_extreme_timestamps_and_delta():
+    """Window tests are differences of timestamps: no overflow near the int64
+    limits, and a span beyond int64 is rejected."""
+    s, d, _ = synth.random_small(6, 6, 40, 1)
+    rng = np.random.default_rng(4)
+    t = -(2 ** 62) + rng.integers(0, 20, size=40).astype(np.int64) * (2 ** 58)
+    for delta in (0, 2 ** 58, 2 ** 60, 2 ** 63 - 1):
+        _check_against_brute(s, d, t, delta)
+    with pytest.raises(ValueError):
+        oracle.Graph(np.array([0, 1]), np.array([1, 0]), np.array([-(2 ** 63), 2 ** 63 - 1]))
+
+
 def test_empty_graph():
     G = oracle.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
     star, pair, tri = G.count(5)

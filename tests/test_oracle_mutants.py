@@ -32,7 +32,7 @@ MUTANTS = {
     "alg2_raw_time_order": ("} else if (before(ei.t, ei.id, ek.t, ek.id) && before(ek.t, ek.id, ej.t, ej.id)) {",
                             "} else if (ei.t <= ek.t && ek.t <= ej.t) {"),
     "alg2_dir_k_wrt_w": ("const int dk = ek.src == v ? O : IN;", "const int dk = ek.src == w ? O : IN;"),
-    "alg2_type_III_window": ("&& ek.t <= ei.t + delta) {", "&& ek.t <= ej.t + delta) {"),
+    "alg2_type_III_window": ("&& ek.t - ei.t <= delta) {", "&& ek.t - ej.t <= delta) {"),
     "alg2_tri_transposed": ("TRI(T_II, ei.dir, ej.dir, dk)++;", "TRI(T_II, ej.dir, ei.dir, dk)++;"),
     # the definitions
     "brute_star_type": ("const int iso = s12 ? 0 : (s02 ? 1 : 2);", "const int iso = s12 ? 2 : (s02 ? 1 : 0);"),
