@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--cpu-sample-days", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-count-only", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -264,20 +265,22 @@ def main():
                 "algo_bytes_per_edge": ALGO_BYTES[dom]}
 
     # count only (graph resident)
-    g = tm.build_async(src, dst, tt, stream)
+    count_ms = None
+    g = tm.build_async(src, dst, tt, stream) if not args.no_count_only else None
     torch.cuda.synchronize()
-    for _ in range(2):
-        tm.count_async(g, delta, cells, stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        tm.count_async(g, delta, cells, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    count_ms = e0.elapsed_time(e1) / args.steps
+    if g is not None:
+        for _ in range(2):
+            tm.count_async(g, delta, cells, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tm.count_async(g, delta, cells, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        count_ms = e0.elapsed_time(e1) / args.steps
+        g.free_async(stream)
+        torch.cuda.synchronize()
     out_cells = cells.cpu().numpy()
-    g.free_async(stream)
-    torch.cuda.synchronize()
     _, bad = tm.merge(out_cells)
 
     e2e = None
@@ -319,7 +322,8 @@ def main():
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": launches,
-            "count_only": {"value": m / (count_ms / 1e3), "unit": UNIT, "ms": count_ms},
+            "count_only": ({"value": m / (count_ms / 1e3), "unit": UNIT, "ms": count_ms}
+                           if count_ms else None),
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "isomorphism_mismatches": bad,
         }))

@@ -67,30 +67,27 @@ __global__ void k_validation_init(Validation *v) {
 }
 
 template <typename K>
-__global__ void k_time_keys(const int64_t *__restrict__ t, int64_t m, long long tmin,
-                            K *__restrict__ keys, uint32_t *__restrict__ vals) {
+__global__ void k_time_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                            const int64_t *__restrict__ t, int64_t m, long long tmin,
+                            K *__restrict__ keys, uint64_t *__restrict__ vals) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         keys[e] = (K)((unsigned long long)t[e] - (unsigned long long)tmin);
-        vals[e] = (uint32_t)e;
+        vals[e] = ((uint64_t)(uint32_t)src[e] << 32) | (uint32_t)dst[e];
     }
 }
 
 // Edges in rank order: rank i -> (src, dst, relative t).
 template <typename K>
-__global__ void k_rank_edges(const K *__restrict__ tkey, const uint32_t *__restrict__ perm,
-                             const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+__global__ void k_rank_edges(const K *__restrict__ tkey, const uint64_t *__restrict__ sd,
                              int64_t m, int32_t *__restrict__ esrc, int32_t *__restrict__ edst,
-                             int64_t *__restrict__ et, int32_t *__restrict__ deg) {
+                             int64_t *__restrict__ et) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t e = perm[i];
-        int32_t a = src[e], b = dst[e];
-        esrc[i] = a;
-        edst[i] = b;
+        const uint64_t v = sd[i];
+        esrc[i] = (int32_t)(v >> 32);
+        edst[i] = (int32_t)(uint32_t)v;
         et[i] = (int64_t)tkey[i];
-        atomicAdd(&deg[a], 1);
-        atomicAdd(&deg[b], 1);
     }
 }
 
@@ -107,6 +104,17 @@ __global__ void k_entry_keys(const int32_t *__restrict__ esrc, const int32_t *__
     }
 }
 
+// off[u] = first position of centre u in the centre-sorted entries.
+__global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64_t n,
+                          int32_t *__restrict__ off) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = p == 0 ? 0 : (int64_t)centre[p - 1] + 1;
+        const int64_t hi = p == n2 ? n : (int64_t)centre[p];
+        for (int64_t u = lo; u <= hi; u++) off[u] = (int32_t)p;
+    }
+}
+
 __global__ void k_dir_flags(const uint32_t *__restrict__ code, int64_t n2, int32_t *__restrict__ f) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -117,15 +125,16 @@ __global__ void k_fill_T(const uint32_t *__restrict__ centre, const uint32_t *__
                          const int32_t *__restrict__ cin, const int32_t *__restrict__ esrc,
                          const int32_t *__restrict__ edst, const int64_t *__restrict__ et,
                          int64_t n2, TEnt *__restrict__ T, int32_t *__restrict__ pos_src,
-                         int32_t *__restrict__ pos_dst) {
+                         int32_t *__restrict__ pos_dst, int32_t *__restrict__ minflag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c = code[p];
         int32_t rank = (int32_t)(c >> 1);
         int side = (int)(c & 1u);
+        const uint32_t nbr = (uint32_t)(side ? esrc[rank] : edst[rank]);
         TEnt e;
         e.t = et[rank];
-        e.nbr = (uint32_t)(side ? esrc[rank] : edst[rank]) | ((uint32_t)side << 31);
+        e.nbr = nbr | ((uint32_t)side << 31);
         e.rank = rank;
         e.cin = cin[p];
         e.prev = -1;
@@ -134,50 +143,61 @@ __global__ void k_fill_T(const uint32_t *__restrict__ centre, const uint32_t *__
         T[p] = e;
         if (side) pos_dst[rank] = (int32_t)p;
         else pos_src[rank] = (int32_t)p;
+        minflag[p] = centre[p] < nbr ? 1 : 0;
     }
 }
 
-template <typename K>
-__global__ void k_pair_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
-                            int64_t m, int nb, K *__restrict__ keys, uint32_t *__restrict__ vals) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t a = (uint32_t)esrc[i], b = (uint32_t)edst[i];
-        uint32_t lo = min(a, b), hi = max(a, b);
-        keys[i] = ((K)lo << nb) | (K)hi;
-        vals[i] = (uint32_t)i;
+// The entries at the smaller endpoint of each edge, keyed by the larger one.
+// In T order (centre, then rank); a stable sort by the key then yields every
+// node pair's edges as one run in rank order.
+__global__ void k_pair_compact(const TEnt *__restrict__ T, const int32_t *__restrict__ minflag,
+                               const int32_t *__restrict__ idx, int64_t n2,
+                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (minflag[p]) {
+            const int32_t k = idx[p];
+            keys[k] = T[p].nbr & 0x7fffffffu;
+            vals[k] = (uint32_t)p;
+        }
     }
 }
 
-template <typename K>
-__global__ void k_pair_flags(const K *__restrict__ pkey, const uint32_t *__restrict__ pl,
-                             const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
-                             int64_t m, int32_t *__restrict__ rank_out,
+// Pair list k: the edge's rank, whether its source is the smaller id, and
+// whether k starts a new node pair.
+__global__ void k_pair_flags(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ ppos,
+                             const TEnt *__restrict__ T, int64_t m, int2 *__restrict__ pl,
                              int32_t *__restrict__ srcmin, int32_t *__restrict__ head) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t r = pl[k];
-        rank_out[k] = (int32_t)r;
-        srcmin[k] = esrc[r] < edst[r] ? 1 : 0;
-        head[k] = (k == 0 || pkey[k] != pkey[k - 1]) ? 1 : 0;
+        const TEnt e = T[ppos[k]];
+        pl[k].x = e.rank;
+        srcmin[k] = (e.nbr >> 31) ? 0 : 1;  // o at the smaller endpoint: it is the source
+        head[k] = (k == 0 || pkey[k] != pkey[k - 1] || e.centre != T[ppos[k - 1]].centre) ? 1 : 0;
     }
 }
 
 // Consecutive edges of one node pair are consecutive same-neighbour entries
 // at both of its nodes: link their entries.
-template <typename K>
-__global__ void k_links(const K *__restrict__ pkey, const int32_t *__restrict__ pl_rank,
-                        const int32_t *__restrict__ esrc, const int32_t *__restrict__ pos_src,
-                        const int32_t *__restrict__ pos_dst, int64_t m, TEnt *__restrict__ T) {
+__global__ void k_pair_cum(const int32_t *__restrict__ cum, int64_t m, int2 *__restrict__ pl) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        pl[k].y = cum[k];
+        if (k == m) pl[k].x = INT_MAX;
+    }
+}
+
+__global__ void k_links(const uint32_t *__restrict__ ppos, const int32_t *__restrict__ head,
+                        const int2 *__restrict__ pl, const int32_t *__restrict__ srcmin,
+                        const int32_t *__restrict__ pos_src, const int32_t *__restrict__ pos_dst,
+                        int64_t m, TEnt *__restrict__ T) {
     for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
-        if (pkey[k] != pkey[k - 1]) continue;
-        int32_t r = pl_rank[k], rp = pl_rank[k - 1];
-        // node `esrc[r]`: e_k sits at its source; e_{k-1} at whichever side is that node
-        int32_t c0 = esrc[r];
-        int32_t cur0 = pos_src[r], cur1 = pos_dst[r];
-        int32_t prv0 = esrc[rp] == c0 ? pos_src[rp] : pos_dst[rp];
-        int32_t prv1 = esrc[rp] == c0 ? pos_dst[rp] : pos_src[rp];
+        if (head[k]) continue;
+        const int32_t cur0 = (int32_t)ppos[k], prv0 = (int32_t)ppos[k - 1];
+        const int32_t r = pl[k].x, rp = pl[k - 1].x;
+        const int32_t cur1 = srcmin[k] ? pos_dst[r] : pos_src[r];      // larger endpoint
+        const int32_t prv1 = srcmin[k - 1] ? pos_dst[rp] : pos_src[rp];
         T[cur0].prev = prv0;
         T[prv0].next = cur0;
         T[cur1].prev = prv1;
@@ -185,11 +205,8 @@ __global__ void k_links(const K *__restrict__ pkey, const int32_t *__restrict__ 
     }
 }
 
-template <typename K>
-__global__ void k_run_begins(const K *__restrict__ pkey, const int32_t *__restrict__ head,
-                              const int32_t *__restrict__ run_id, const int32_t *__restrict__ pl_rank,
-                              const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
-                              int64_t m, int32_t *__restrict__ run_begin) {
+__global__ void k_run_begins(const int32_t *__restrict__ head, const int32_t *__restrict__ run_id,
+                             int64_t m, int32_t *__restrict__ run_begin) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (head[k]) run_begin[run_id[k]] = (int32_t)k;
@@ -197,15 +214,20 @@ __global__ void k_run_begins(const K *__restrict__ pkey, const int32_t *__restri
 }
 
 __global__ void k_hash_fill(const int32_t *__restrict__ run_begin, int64_t nruns, int64_t m,
-                            const int32_t *__restrict__ pl_rank, const int32_t *__restrict__ esrc,
-                            const int32_t *__restrict__ edst, PairSlot *__restrict__ H,
+                            const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ ppos,
+                            const TEnt *__restrict__ T, const int2 *__restrict__ pl,
+                            const int32_t *__restrict__ srcmin, PairSlot *__restrict__ H,
                             uint32_t mask) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nruns;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t b = run_begin[j];
         int32_t e = j + 1 < nruns ? run_begin[j + 1] : (int32_t)m;
-        int32_t r = pl_rank[b];
-        uint64_t key = pair_key((uint32_t)esrc[r], (uint32_t)edst[r]);
+        const uint64_t key = pair_key((uint32_t)T[ppos[b]].centre, pkey[b]);
+        if (e - b == 1) {  // single edge: kept in the slot
+            const int32_t f = srcmin[b];
+            b = -(pl[b].x + 1);
+            e = f;
+        }
         uint32_t h = hash_pair(key) & mask;
         for (uint32_t probe = 0; probe <= mask; probe++) {
             unsigned long long prev =
@@ -245,27 +267,27 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <typename K>
-void build_pairs(DevGraph &g, const int32_t *esrc, const int32_t *edst, int nb, cudaStream_t s) {
-    const int64_t m = g.m;
-    K *pk = dev_alloc_n<K>(m, s), *pk2 = dev_alloc_n<K>(m, s);
-    uint32_t *pv = dev_alloc_n<uint32_t>(m, s), *pv2 = dev_alloc_n<uint32_t>(m, s);
-    TM_LAUNCH(k_pair_keys<K>, grid_for(m), 256, 0, s, esrc, edst, m, nb, pk, pv);
-    K *sk;
-    uint32_t *sv;
-    if constexpr (sizeof(K) == 4)
-        radix_sort_u32(pk, pv, pk2, pv2, m, 2 * nb, s, &sk, &sv);
-    else
-        radix_sort_u64(pk, pv, pk2, pv2, m, 2 * nb, s, &sk, &sv);
+void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
+    const int64_t m = g.m, n2 = 2 * m;
+    int32_t *idx = dev_alloc_n<int32_t>(n2 + 1, s);
+    exclusive_scan_i32(minflag, idx, n2, s);
+    uint32_t *k1 = dev_alloc_n<uint32_t>(m, s), *k2 = dev_alloc_n<uint32_t>(m, s);
+    uint32_t *v1 = dev_alloc_n<uint32_t>(m, s), *v2 = dev_alloc_n<uint32_t>(m, s);
+    TM_LAUNCH(k_pair_compact, grid_for(n2), 256, 0, s, g.T, minflag, idx, n2, k1, v1);
+    dev_free(idx, s);
+    uint32_t *sk, *sv;
+    radix_sort_u32(k1, v1, k2, v2, m, nb, s, &sk, &sv);
 
     int32_t *srcmin = dev_alloc_n<int32_t>(m, s);
     int32_t *head = dev_alloc_n<int32_t>(m, s);
     int32_t *run_id = dev_alloc_n<int32_t>(m + 1, s);
-    TM_LAUNCH(k_pair_flags<K>, grid_for(m), 256, 0, s, sk, sv, esrc, edst, m, g.pl_rank, srcmin,
-              head);
-    exclusive_scan_i32(srcmin, g.pl_cum, m, s);
+    int32_t *cum = dev_alloc_n<int32_t>(m + 1, s);
+    TM_LAUNCH(k_pair_flags, grid_for(m), 256, 0, s, sk, sv, g.T, m, g.pl, srcmin, head);
+    exclusive_scan_i32(srcmin, cum, m, s);
+    TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, s, cum, m, g.pl);
+    dev_free(cum, s);
     exclusive_scan_i32(head, run_id, m, s);
-    TM_LAUNCH(k_links<K>, grid_for(m), 256, 0, s, sk, g.pl_rank, esrc, g.pos_src, g.pos_dst, m,
+    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pl, srcmin, g.pos_src, g.pos_dst, m,
               g.T);
     int32_t nruns = 0;
     TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -276,35 +298,33 @@ void build_pairs(DevGraph &g, const int32_t *esrc, const int32_t *edst, int nb, 
     g.hash_mask = (uint32_t)(cap - 1);
     TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * cap, s));
     int32_t *run_begin = dev_alloc_n<int32_t>(nruns + 1, s);
-    TM_LAUNCH(k_run_begins<K>, grid_for(m), 256, 0, s, sk, head, run_id, g.pl_rank, esrc, edst,
-              m, run_begin);
-    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, g.pl_rank,
-              esrc, edst, g.hash, g.hash_mask);
+    TM_LAUNCH(k_run_begins, grid_for(m), 256, 0, s, head, run_id, m, run_begin);
+    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, sk, sv, g.T,
+              g.pl, srcmin, g.hash, g.hash_mask);
     dev_free(run_begin, s);
     dev_free(run_id, s);
     dev_free(head, s);
     dev_free(srcmin, s);
-    dev_free(pk, s);
-    dev_free(pk2, s);
-    dev_free(pv, s);
-    dev_free(pv2, s);
+    dev_free(k1, s);
+    dev_free(k2, s);
+    dev_free(v1, s);
+    dev_free(v2, s);
 }
 
 template <typename K>
 void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
-                  int keybits, int32_t *esrc, int32_t *edst, int64_t *et, int32_t *deg,
-                  cudaStream_t s) {
+                  int keybits, int32_t *esrc, int32_t *edst, int64_t *et, cudaStream_t s) {
     const int64_t m = g.m;
     K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
-    uint32_t *v1 = dev_alloc_n<uint32_t>(m, s), *v2 = dev_alloc_n<uint32_t>(m, s);
-    TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, t, m, (long long)g.tmin, k1, v1);
+    uint64_t *v1 = dev_alloc_n<uint64_t>(m, s), *v2 = dev_alloc_n<uint64_t>(m, s);
+    TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin, k1, v1);
     K *sk;
-    uint32_t *sv;
+    uint64_t *sv;
     if constexpr (sizeof(K) == 4)
-        radix_sort_u32(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+        radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
     else
-        radix_sort_u64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-    TM_LAUNCH(k_rank_edges<K>, grid_for(m), 256, 0, s, sk, sv, src, dst, m, esrc, edst, et, deg);
+        radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+    TM_LAUNCH(k_rank_edges<K>, grid_for(m), 256, 0, s, sk, sv, m, esrc, edst, et);
     dev_free(k1, s);
     dev_free(k2, s);
     dev_free(v1, s);
@@ -318,8 +338,7 @@ void free_graph(DevGraph &g, cudaStream_t s) {
     dev_free(g.off, s);
     dev_free(g.pos_src, s);
     dev_free(g.pos_dst, s);
-    dev_free(g.pl_rank, s);
-    dev_free(g.pl_cum, s);
+    dev_free(g.pl, s);
     dev_free(g.hash, s);
     g = DevGraph();
 }
@@ -392,11 +411,10 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     g.T = dev_alloc_n<TEnt>(2 * m, s);
     g.pos_src = dev_alloc_n<int32_t>(m, s);
     g.pos_dst = dev_alloc_n<int32_t>(m, s);
-    g.pl_rank = dev_alloc_n<int32_t>(m, s);
-    g.pl_cum = dev_alloc_n<int32_t>(m + 1, s);
+    g.pl = dev_alloc_n<int2>(m + 1, s);
     if (m == 0) {
         TM_CUDA(cudaMemsetAsync(g.off, 0, sizeof(int32_t) * (n + 1), s));
-        TM_CUDA(cudaMemsetAsync(g.pl_cum, 0, sizeof(int32_t), s));
+        TM_CUDA(cudaMemsetAsync(g.pl, 0, sizeof(int2), s));
         g.hash = dev_alloc_n<PairSlot>(16, s);
         g.hash_mask = 15;
         TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * 16, s));
@@ -407,34 +425,32 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     // 2. rank order
     int32_t *esrc = dev_alloc_n<int32_t>(m, s), *edst = dev_alloc_n<int32_t>(m, s);
     int64_t *et = dev_alloc_n<int64_t>(m, s);
-    int32_t *deg = dev_alloc_n<int32_t>(n, s);
-    TM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, s));
     const int keybits = bits_for(span);
     {
-    PhaseTimer pt(TM_PH_TIME_SORT, s);
-    if (keybits <= 32)
-        sort_by_time<uint32_t>(src, dst, t, g, keybits, esrc, edst, et, deg, s);
-    else
-        sort_by_time<uint64_t>(src, dst, t, g, keybits, esrc, edst, et, deg, s);
-    release_inputs();
-    exclusive_scan_i32(deg, g.off, n, s);
-    dev_free(deg, s);
+        PhaseTimer pt(TM_PH_TIME_SORT, s);
+        if (keybits <= 32)
+            sort_by_time<uint32_t>(src, dst, t, g, keybits, esrc, edst, et, s);
+        else
+            sort_by_time<uint64_t>(src, dst, t, g, keybits, esrc, edst, et, s);
+        release_inputs();
     }
 
     // 3-4. S_u for every centre
+    const int64_t n2 = 2 * m;
+    int32_t *minflag = dev_alloc_n<int32_t>(n2, s);
     {
         PhaseTimer pt(TM_PH_INCIDENT, s);
-        const int64_t n2 = 2 * m;
         uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
         uint32_t *v1 = dev_alloc_n<uint32_t>(n2, s), *v2 = dev_alloc_n<uint32_t>(n2, s);
         TM_LAUNCH(k_entry_keys, grid_for(n2), 256, 0, s, esrc, edst, m, k1, v1);
         uint32_t *sk, *sv;
         radix_sort_u32(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
+        TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, sk, n2, n, g.off);
         int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
         TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
         exclusive_scan_i32(flags, cin, n2, s);
         TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, esrc, edst, et, n2, g.T,
-                  g.pos_src, g.pos_dst);
+                  g.pos_src, g.pos_dst, minflag);
         dev_free(flags, s);
         dev_free(cin, s);
         dev_free(k1, s);
@@ -443,18 +459,15 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         dev_free(v2, s);
     }
     dev_free(et, s);
-
-    // 5-6. pair list, hash, same-neighbour links
-    const int nb = bits_for((uint64_t)(n - 1));
-    {
-        PhaseTimer pt(TM_PH_PAIRS, s);
-        if (2 * nb <= 32)
-            build_pairs<uint32_t>(g, esrc, edst, nb, s);
-        else
-            build_pairs<uint64_t>(g, esrc, edst, nb, s);
-    }
     dev_free(esrc, s);
     dev_free(edst, s);
+
+    // 5-6. pair list, hash, same-neighbour links
+    {
+        PhaseTimer pt(TM_PH_PAIRS, s);
+        build_pairs(g, minflag, bits_for((uint64_t)(n - 1)), s);
+    }
+    dev_free(minflag, s);
     TM_CUDA(cudaStreamSynchronize(s));
 }
 

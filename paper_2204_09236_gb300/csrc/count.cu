@@ -31,10 +31,14 @@
 // (Sec. IV-B, "counted three times"), so the type-I and type-III cells are
 // filled from type II by the rotation identity
 //   Tri[II,di,dj,dk] = Tri[I,!dk,!dj,!di] = Tri[III,!di,dk,dj].
-// Type II at centre u for the later u-edge e_j = r (node w): the pairs
-// (e_i in W(r) with node x != w, e_k in E_(x,w)) with e_i < e_k < e_j. The
-// kernel enumerates the smaller of W_u(r) and W_w(twin of r) and counts the
-// matching edges of the pair list by binary search on rank.
+// Type II at centre u with later u-edge e_j = (u, w): pairs e_i < e_k < e_j
+// with e_i = (u, x) in W_u(e_j) and e_k = (x, w), which then lies in
+// W_w(e_j). So for each edge e_j the type-II triangles at BOTH of its
+// endpoints are the same-neighbour matches between the two endpoint windows
+// W_u(e_j) and W_w(e_j): a match (a in W_u, k in W_w) with a < k is centred at
+// u, one with k < a at w. k_tri visits each edge once, enumerates the smaller
+// window and finds the matches in the bigger one through the pair list
+// (hash lookup of E_(big, x), binary search on rank).
 #include "tm_internal.cuh"
 
 namespace tmi {
@@ -44,6 +48,16 @@ namespace {
 constexpr int THREADS = 256;
 
 __device__ __forceinline__ int dir_of(uint32_t nbr) { return (int)(nbr >> 31); }
+
+__device__ __forceinline__ int32_t warp_incl_scan_i32(int32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
 __device__ __forceinline__ uint32_t node_of(uint32_t nbr) { return nbr & 0x7fffffffu; }
 
 // First position p in [b, r] with T[p].t >= bound; T[r].t >= bound holds.
@@ -92,15 +106,18 @@ __device__ __forceinline__ int32_t gallop_hi(const TEnt *__restrict__ T, int32_t
 
 // Cells are flat: Star ((T*2+a)*2+b)*2+c at 0..23, Pair (a*2+b)*2+c at
 // 24..31, Tri ((T*2+a)*2+b)*2+c at 32..55.
-template <int NC>
-__device__ void block_flush(const unsigned long long (&acc)[NC], int cell0,
+// Adds acc[SRC + c] (c < NC) of every thread of the block into
+// cells[cell0 + c]: warp shuffles, shared atomics, one global atomic per cell.
+template <int NC, int SRC, int NA>
+__device__ void block_flush(const unsigned long long (&acc)[NA], int cell0,
                             unsigned long long *__restrict__ cells) {
     __shared__ unsigned long long red[NC];
+    __syncthreads();
     if (threadIdx.x < NC) red[threadIdx.x] = 0;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-        unsigned long long v = acc[c];
+        unsigned long long v = acc[SRC + c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&red[c], v);
@@ -122,79 +139,100 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
                                                 int64_t m, int64_t delta, int32_t r,
                                                 const TEnt &e, unsigned long long (&acc)[32]) {
     const int64_t tr = e.t;
-    // backward walk over same-neighbour entries inside W(r)
-    uint64_t n[2] = {0, 0}, c2s[2][2] = {{0, 0}, {0, 0}};
-    uint64_t X[2][2] = {{0, 0}, {0, 0}};   // X[d1][d2]: d2 entries strictly between a and r
-    uint64_t Yp[2][2] = {{0, 0}, {0, 0}};  // Yp[d2][d1]: d1 entries in [S_u begin, b)
-    const int32_t cin_r = e.cin;
-    int32_t a = e.prev, cur = r;
-    bool any = false;
-    while (a >= 0 && a < cur) {  // links strictly decrease: the walk always ends
-        const TEnt ea = T[a];
-        if (tr - ea.t > delta) break;
-        any = true;
-        const int da = dir_of(ea.nbr);
-        // pairs (a, later same-node entries in the window)
-        c2s[da][0] += n[0];
-        c2s[da][1] += n[1];
-        n[da] += 1;
-        const int64_t between_in = (int64_t)cin_r - (ea.cin + da);
-        const int64_t between_o = (int64_t)(r - a - 1) - between_in;
-        X[da][0] += (uint64_t)between_o;
-        X[da][1] += (uint64_t)between_in;
-        Yp[da][0] += (uint64_t)(a - ea.cin);  // C_o(a)
-        Yp[da][1] += (uint64_t)ea.cin;        // C_in(a)
-        cur = a;
-        a = ea.prev;
-    }
     const int32_t u = e.centre;
-    const int32_t seg_end = off[u + 1];
+    const int32_t seg_b = off[u], seg_end = off[u + 1];
+    // W(r) and F(r) bounds from the neighbouring entries of S_u (local reads);
+    // the same-neighbour links are followed only when they land inside.
+    const bool wnd_back = e.prev >= 0 && r > seg_b && tr - T[r - 1].t <= delta;
+    const bool wnd_fwd = e.next >= 0 && r + 1 < seg_end && T[r + 1].t - tr <= delta;
+    if (!wnd_back && !wnd_fwd) return;
     const int64_t cin_end = seg_end < m2 ? (int64_t)T[seg_end].cin : m;
-    if (any) {
-        const int32_t lo = gallop_lo(T, off[u], r, tr - delta);
-        const int64_t cin_lo = T[lo].cin;
-        const int64_t co_lo = (int64_t)lo - cin_lo;
-#pragma unroll
-        for (int d1 = 0; d1 < 2; d1++)
-#pragma unroll
-            for (int d2 = 0; d2 < 2; d2++) {
-                const uint64_t s = c2s[d1][d2];
-                acc[IX(d1, d2, D3)] += s;                                         // Pair
-                acc[16 + IX(d1, d2, D3)] += X[d1][d2] - s;                        // Star-II
-                const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;   // C_d1(lo)
-                acc[8 + IX(d1, d2, D3)] += Yp[d2][d1] - n[d2] * base - s;         // Star-I
-                acc[24 + IX(d1, d2, D3)] -= s;                                    // Star-III
+    if (wnd_back) {
+        const int32_t lo = gallop_lo(T, seg_b, r, tr - delta);
+        if (e.prev >= lo) {
+            // per direction d of the run entries: n_d (count), c2s_{d,d'} (pairs),
+            // X_{d,d'} (d' entries strictly between a and r), Y_{d,d'} (d' entries
+            // before b, as a prefix); kept in scalars so they stay in registers
+            uint64_t n0 = 0, n1 = 0, c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+            uint64_t X00 = 0, X01 = 0, X10 = 0, X11 = 0, Y00 = 0, Y01 = 0, Y10 = 0, Y11 = 0;
+            const int32_t cin_r = e.cin;
+            int32_t a = e.prev, cur = r;
+            while (a >= lo && a < cur) {  // links strictly decrease: the walk always ends
+                const TEnt ea = T[a];
+                const int da = dir_of(ea.nbr);
+                const uint64_t between_in = (uint64_t)((int64_t)cin_r - (ea.cin + da));
+                const uint64_t between_o = (uint64_t)(r - a - 1) - between_in;
+                const uint64_t co_a = (uint64_t)(a - ea.cin), ci_a = (uint64_t)ea.cin;
+                if (da) {  // pairs (a, later same-node entries in the window)
+                    c10 += n0;
+                    c11 += n1;
+                    n1 += 1;
+                    X10 += between_o;
+                    X11 += between_in;
+                    Y10 += co_a;
+                    Y11 += ci_a;
+                } else {
+                    c00 += n0;
+                    c01 += n1;
+                    n0 += 1;
+                    X00 += between_o;
+                    X01 += between_in;
+                    Y00 += co_a;
+                    Y01 += ci_a;
+                }
+                cur = a;
+                a = ea.prev;
             }
-        // Star-III, pairs entering: n_r[d1] x #(d3' entries after r)
-        const int64_t after_in = cin_end - (cin_r + D3);
-        const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
+            const uint64_t n[2] = {n0, n1};
+            const uint64_t c2s[2][2] = {{c00, c01}, {c10, c11}};
+            const uint64_t X[2][2] = {{X00, X01}, {X10, X11}};
+            const uint64_t Yp[2][2] = {{Y00, Y01}, {Y10, Y11}};
+            const int64_t cin_lo = T[lo].cin;
+            const int64_t co_lo = (int64_t)lo - cin_lo;
 #pragma unroll
-        for (int d1 = 0; d1 < 2; d1++) {
-            acc[24 + IX(d1, D3, 0)] += n[d1] * (uint64_t)after_o;
-            acc[24 + IX(d1, D3, 1)] += n[d1] * (uint64_t)after_in;
+            for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+                for (int d2 = 0; d2 < 2; d2++) {
+                    const uint64_t sp = c2s[d1][d2];
+                    acc[IX(d1, d2, D3)] += sp;                                       // Pair
+                    acc[16 + IX(d1, d2, D3)] += X[d1][d2] - sp;                      // Star-II
+                    const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;  // C_d1(lo)
+                    acc[8 + IX(d1, d2, D3)] += Yp[d2][d1] - n[d2] * base - sp;       // Star-I
+                    acc[24 + IX(d1, d2, D3)] -= sp;                                  // Star-III
+                }
+            // Star-III, pairs entering: n_r[d1] x #(d3' entries after r)
+            const int64_t after_in = cin_end - (cin_r + D3);
+            const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
+#pragma unroll
+            for (int d1 = 0; d1 < 2; d1++) {
+                acc[24 + IX(d1, D3, 0)] += n[d1] * (uint64_t)after_o;
+                acc[24 + IX(d1, D3, 1)] += n[d1] * (uint64_t)after_in;
+            }
         }
     }
-    // forward walk: same-neighbour entries inside F(r) (pairs leaving)
-    int32_t b = e.next;
-    uint64_t f[2] = {0, 0};
-    cur = r;
-    while (b > cur && b < m2) {  // links strictly increase: the walk always ends
-        const TEnt eb = T[b];
-        if (eb.t - tr > delta) break;
-        f[dir_of(eb.nbr)] += 1;
-        cur = b;
-        b = eb.next;
-    }
-    if (f[0] + f[1]) {
+    if (wnd_fwd) {
         const int32_t hi = gallop_hi(T, r, seg_end, tr, delta);
-        const TEnt eh = T[hi];
-        const int64_t cin_h1 = (int64_t)eh.cin + dir_of(eh.nbr);  // C_in(hi+1)
-        const int64_t after_in = cin_end - cin_h1;
-        const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
+        if (e.next <= hi) {
+            // same-neighbour entries inside F(r): pairs leaving after hi(r)
+            uint64_t f0 = 0, f1 = 0;
+            int32_t b = e.next, cur = r;
+            while (b > cur && b <= hi) {  // links strictly increase: the walk always ends
+                const TEnt eb = T[b];
+                if (dir_of(eb.nbr)) f1 += 1;
+                else f0 += 1;
+                cur = b;
+                b = eb.next;
+            }
+            const uint64_t f[2] = {f0, f1};
+            const TEnt eh = T[hi];
+            const int64_t cin_h1 = (int64_t)eh.cin + dir_of(eh.nbr);  // C_in(hi+1)
+            const int64_t after_in = cin_end - cin_h1;
+            const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
 #pragma unroll
-        for (int d2 = 0; d2 < 2; d2++) {
-            acc[24 + IX(D3, d2, 0)] -= f[d2] * (uint64_t)after_o;
-            acc[24 + IX(D3, d2, 1)] -= f[d2] * (uint64_t)after_in;
+            for (int d2 = 0; d2 < 2; d2++) {
+                acc[24 + IX(D3, d2, 0)] -= f[d2] * (uint64_t)after_o;
+                acc[24 + IX(D3, d2, 1)] -= f[d2] * (uint64_t)after_in;
+            }
         }
     }
 }
@@ -214,18 +252,12 @@ __global__ void __launch_bounds__(THREADS)
         else star_pair_entry<0>(T, off, m2, m, delta, r, e, acc);
     }
     // acc order: Pair, Star-I, Star-II, Star-III -> cells Star[T] at 0.., Pair at 24..
-    unsigned long long star[24], pair[8];
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        pair[c] = acc[c];
-        star[c] = acc[8 + c];
-        star[8 + c] = acc[16 + c];
-        star[16 + c] = acc[24 + c];
-    }
-    block_flush<24>(star, 0, cells);
-    block_flush<8>(pair, 24, cells);
+    block_flush<24, 8>(acc, 0, cells);
+    block_flush<8, 0>(acc, 24, cells);
 }
 
+// Raw hash slot of a node pair: (begin, end) of its run, the single edge
+// encoded in the slot (begin < 0), or (0, 0) if the pair has no edge.
 __device__ __forceinline__ int2 find_pair(const PairSlot *__restrict__ H, uint32_t mask,
                                           uint64_t key) {
     uint32_t h = hash_pair(key) & mask;
@@ -238,96 +270,229 @@ __device__ __forceinline__ int2 find_pair(const PairSlot *__restrict__ H, uint32
     return make_int2(0, 0);
 }
 
-// First index in [b, e) with pl_rank >= x.
-__device__ __forceinline__ int32_t lower_rank(const int32_t *__restrict__ pl, int32_t b, int32_t e,
+// First index in [b, e) with pl[].x >= x.
+__device__ __forceinline__ int32_t lower_rank(const int2 *__restrict__ pl, int32_t b, int32_t e,
                                               int32_t x) {
     while (b < e) {
         int32_t mid = b + ((e - b) >> 1);
-        if (pl[mid] < x) b = mid + 1;
+        if (pl[mid].x < x) b = mid + 1;
         else e = mid;
     }
     return b;
 }
 
-template <int DJ>
-__device__ __forceinline__ void tri_entry(const DevGraph &g, int64_t delta, int32_t r,
-                                          const TEnt &e, unsigned long long (&acc)[8]) {
-    const TEnt *__restrict__ T = g.T;
-    const int64_t tj = e.t;
-    const uint32_t u = (uint32_t)e.centre, w = node_of(e.nbr);
-    const int32_t lo_u = gallop_lo(T, g.off[u], r, tj - delta);
-    const int32_t wu = r - lo_u;
-    if (wu == 0) return;
-    const int32_t twin = DJ == 0 ? g.pos_dst[e.rank] : g.pos_src[e.rank];
-    const int32_t lo_w = gallop_lo(T, g.off[w], twin, tj - delta);
-    const int32_t ww = twin - lo_w;
-    if (ww == 0) return;
-    if (wu <= ww) {
-        // e_i in W_u(r), e_k in E_(x, w) with rank_i < rank_k < rank_j
-        for (int32_t a = lo_u; a < r; a++) {
-            const TEnt ea = T[a];
-            const uint32_t x = node_of(ea.nbr);
-            if (x == w) continue;
-            const int2 run = find_pair(g.hash, g.hash_mask, pair_key(x, w));
-            if (run.x == run.y) continue;
-            const int32_t k0 = lower_rank(g.pl_rank, run.x, run.y, ea.rank + 1);
-            const int32_t k1 = lower_rank(g.pl_rank, k0, run.y, e.rank);
-            const int32_t cnt = k1 - k0;
-            if (cnt == 0) continue;
-            const int32_t fmin = g.pl_cum[k1] - g.pl_cum[k0];  // edges whose source is min(x, w)
-            const int32_t from_x = x < w ? fmin : cnt - fmin;   // e_k = x -> w: o w.r.t. x
-            const int di = dir_of(ea.nbr);
-            if (di) {
-                acc[IX(1, DJ, 0)] += (unsigned long long)from_x;
-                acc[IX(1, DJ, 1)] += (unsigned long long)(cnt - from_x);
-            } else {
-                acc[IX(0, DJ, 0)] += (unsigned long long)from_x;
-                acc[IX(0, DJ, 1)] += (unsigned long long)(cnt - from_x);
-            }
+// Edges of E_(big, x) inside [rank_lo, rank_hi), split at rank `at`:
+// nb / na = how many lie before / after `at`, fb / fa = how many of those have
+// the smaller node id as source.
+struct PairCounts {
+    int32_t nb, na, fb, fa;
+};
+
+__device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int32_t rank_lo,
+                                            int32_t rank_hi, int32_t at, PairCounts &c) {
+    const int2 run = find_pair(g.hash, g.hash_mask, key);
+    if (run.x < 0) {  // single edge kept in the slot
+        const int32_t r1 = -run.x - 1;
+        if (r1 < rank_lo || r1 >= rank_hi) return false;
+        const bool before = r1 < at;
+        c.nb = before;
+        c.na = !before;
+        c.fb = before ? run.y : 0;
+        c.fa = before ? 0 : run.y;
+        return true;
+    }
+    if (run.x == run.y) return false;
+    const int32_t k0 = lower_rank(g.pl, run.x, run.y, rank_lo);
+    const int32_t k1 = lower_rank(g.pl, k0, run.y, rank_hi);
+    if (k0 == k1) return false;
+    const int32_t ks = lower_rank(g.pl, k0, k1, at);
+    const int32_t c0 = g.pl[k0].y, cs = g.pl[ks].y, c1 = g.pl[k1].y;
+    c.nb = ks - k0;
+    c.na = k1 - ks;
+    c.fb = cs - c0;
+    c.fa = c1 - cs;
+    return true;
+}
+
+// The join of one edge e_j = u -> w (u its source): the smaller of the two
+// endpoint windows is enumerated, the matches are looked up in the other.
+struct TriEdge {
+    uint32_t u, w;
+    int32_t rank_j;
+    int32_t small_lo;     // smaller window: T[small_lo, small_lo + work)
+    int32_t work;
+    int32_t rank_lo_big;  // rank of the first entry of the bigger window
+    int32_t small_is_u;   // 1: the smaller window is W_u
+    int32_t pad;
+};
+
+// Tri type-II cells: acc[IX(di, dj, dk)]. At the source u, e_j is outward
+// (dj = 0); at the destination w it is inward (dj = 1). A match ranked after
+// the item is centred at the item's centre, one ranked before it at the big
+// window's centre.
+__device__ __forceinline__ void tri_probe(const DevGraph &g, const TriEdge &E, const TEnt &it,
+                                          unsigned long long (&acc)[8]) {
+    const uint32_t x = node_of(it.nbr);
+    const uint32_t big = E.small_is_u ? E.w : E.u;
+    if (x == big) return;  // an edge of the pair (u, w) itself
+    PairCounts c;
+    if (!pair_counts(g, pair_key(big, x), E.rank_lo_big, E.rank_j, it.rank, c)) return;
+    // a big-side edge big -> x is outward at big and inward at x
+    const bool big_is_min = big < x;
+    const int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
+    const int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
+    const int di = dir_of(it.nbr);                              // item w.r.t. its centre
+    if (E.small_is_u) {
+        // item a in W_u (node x), matches k in W_w.
+        // after a: centre u, (e_i = a, e_k = k): Tri[II][d_a][0][dir of k w.r.t. x]
+        // before a: centre w, (e_i = k, e_k = a): Tri[II][dir of k w.r.t. w][1][dir of a w.r.t. x]
+        if (di) {
+            acc[IX(1, 0, 0)] += (unsigned long long)(c.na - a_out_big);  // k: x -> w, o at x
+            acc[IX(1, 0, 1)] += (unsigned long long)a_out_big;
+            acc[IX(0, 1, 0)] += (unsigned long long)b_out_big;          // a: x -> u, o at x
+            acc[IX(1, 1, 0)] += (unsigned long long)(c.nb - b_out_big);
+        } else {
+            acc[IX(0, 0, 0)] += (unsigned long long)(c.na - a_out_big);
+            acc[IX(0, 0, 1)] += (unsigned long long)a_out_big;
+            acc[IX(0, 1, 1)] += (unsigned long long)b_out_big;          // a: u -> x, in at x
+            acc[IX(1, 1, 1)] += (unsigned long long)(c.nb - b_out_big);
         }
     } else {
-        // e_k in W_w(twin) with node x != u; e_i in E_(u, x) at positions >= lo_u
-        // of S_u, i.e. rank >= rank(T[lo_u]), and rank_i < rank_k
-        const int32_t rank_lo = T[lo_u].rank;
-        for (int32_t k = lo_w; k < twin; k++) {
-            const TEnt ek = T[k];
-            const uint32_t x = node_of(ek.nbr);
-            if (x == u) continue;
-            const int2 run = find_pair(g.hash, g.hash_mask, pair_key(u, x));
-            if (run.x == run.y) continue;
-            const int32_t k0 = lower_rank(g.pl_rank, run.x, run.y, rank_lo);
-            const int32_t k1 = lower_rank(g.pl_rank, k0, run.y, ek.rank);
-            const int32_t cnt = k1 - k0;
-            if (cnt == 0) continue;
-            const int32_t fmin = g.pl_cum[k1] - g.pl_cum[k0];
-            const int32_t from_u = u < x ? fmin : cnt - fmin;  // e_i = u -> x: o w.r.t. u
-            const int dk = 1 - dir_of(ek.nbr);                  // e_k w.r.t. x
-            if (dk) {
-                acc[IX(0, DJ, 1)] += (unsigned long long)from_u;
-                acc[IX(1, DJ, 1)] += (unsigned long long)(cnt - from_u);
-            } else {
-                acc[IX(0, DJ, 0)] += (unsigned long long)from_u;
-                acc[IX(1, DJ, 0)] += (unsigned long long)(cnt - from_u);
-            }
+        // item k in W_w (node x), matches a in W_u.
+        // before k: centre u, (e_i = a, e_k = k): Tri[II][dir of a w.r.t. u][0][dir of k w.r.t. x]
+        // after k: centre w, (e_i = k, e_k = a): Tri[II][d_k][1][dir of a w.r.t. x]
+        if (di) {
+            acc[IX(0, 0, 0)] += (unsigned long long)b_out_big;          // k: x -> w, o at x
+            acc[IX(1, 0, 0)] += (unsigned long long)(c.nb - b_out_big);
+            acc[IX(1, 1, 0)] += (unsigned long long)(c.na - a_out_big);  // a: x -> u, o at x
+            acc[IX(1, 1, 1)] += (unsigned long long)a_out_big;
+        } else {
+            acc[IX(0, 0, 1)] += (unsigned long long)b_out_big;
+            acc[IX(1, 0, 1)] += (unsigned long long)(c.nb - b_out_big);
+            acc[IX(0, 1, 0)] += (unsigned long long)(c.na - a_out_big);
+            acc[IX(0, 1, 1)] += (unsigned long long)a_out_big;
         }
     }
 }
 
+constexpr int TRI_WARPS = THREADS / 32;
+
+// Walks S_u entries in order; each edge is taken once, at its source entry
+// (direction o). Each edge e_j = (u -> w) is the later centre edge of the
+// type-II triangles at u and at w, whose other centre edges lie in the
+// windows W_u(e_j) and W_w(e_j), so one join of the two windows on the
+// neighbour node counts both. The probes of the 32 edges of a warp are
+// flattened into one list that all lanes share, so a lane never waits for
+// another lane's long window.
 __global__ void __launch_bounds__(THREADS)
     k_tri(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
           unsigned long long *__restrict__ cells) {
+    __shared__ TriEdge edges[TRI_WARPS][32];
+    __shared__ int32_t incl[TRI_WARPS][32];
     unsigned long long acc[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
+    const TEnt *__restrict__ T = g.T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = begin + blockIdx.x * (int64_t)blockDim.x + warp * 32; base < end;
+         base += stride) {
+        const int64_t r = base + lane;
+        TriEdge E;
+        E.work = 0;
+        if (r < end) {
+            const TEnt e = T[r];
+            if (dir_of(e.nbr) == 0) {
+                const uint32_t u = (uint32_t)e.centre;
+                const int32_t sb = g.off[u];
+                if (r > sb && e.t - T[r - 1].t <= delta) {
+                    const uint32_t w = node_of(e.nbr);
+                    const int32_t twin = g.pos_dst[e.rank];
+                    const int32_t wb = g.off[w];
+                    if (twin > wb && e.t - T[twin - 1].t <= delta) {
+                        const int32_t lo_u = gallop_lo(T, sb, (int32_t)r, e.t - delta);
+                        const int32_t lo_w = gallop_lo(T, wb, twin, e.t - delta);
+                        const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
+                        E.u = u;
+                        E.w = w;
+                        E.rank_j = e.rank;
+                        E.small_is_u = wu <= ww;
+                        E.small_lo = E.small_is_u ? lo_u : lo_w;
+                        E.work = E.small_is_u ? wu : ww;
+                        E.rank_lo_big = T[E.small_is_u ? lo_w : lo_u].rank;
+                    }
+                }
+            }
+        }
+        const int32_t inc = warp_incl_scan_i32(E.work);
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0) continue;
+        edges[warp][lane] = E;
+        incl[warp][lane] = inc;
+        __syncwarp();
+        for (int32_t jb = 0; jb < total; jb += 32) {
+            const int32_t j = jb + lane;
+            if (j < total) {
+                // owner: the first lane whose inclusive prefix exceeds j
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (incl[warp][mid] > j) hi = mid;
+                    else lo = mid + 1;
+                }
+                const TriEdge &B = edges[warp][lo];
+                const int32_t k = j - (incl[warp][lo] - B.work);
+                tri_probe(g, B, T[B.small_lo + k], acc);
+            }
+        }
+        __syncwarp();
+    }
+    // type II lives at Tri cells 8..15 (T = 1)
+    block_flush<8, 0>(acc, 32 + 8, cells);
+}
+
+// Type II at the listed centres only: the entries of one centre, each as the
+// later centre edge e_j, joined with the window of its other endpoint; only
+// the matches whose type-II centre is this centre are counted.
+__global__ void __launch_bounds__(THREADS)
+    k_tri_centre(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
+                 unsigned long long *__restrict__ cells) {
+    unsigned long long acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0;
+    const TEnt *__restrict__ T = g.T;
     for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = (int32_t)i;
-        const TEnt e = g.T[r];
-        if (dir_of(e.nbr)) tri_entry<1>(g, delta, r, e, acc);
-        else tri_entry<0>(g, delta, r, e, acc);
+        const TEnt e = T[r];
+        const int dj = dir_of(e.nbr);
+        const uint32_t u = (uint32_t)e.centre, w = node_of(e.nbr);
+        const int32_t lo_u = gallop_lo(T, g.off[u], r, e.t - delta);
+        if (lo_u == r) continue;
+        const int32_t twin = dj ? g.pos_src[e.rank] : g.pos_dst[e.rank];
+        const int32_t lo_w = gallop_lo(T, g.off[w], twin, e.t - delta);
+        if (lo_w == twin) continue;
+        const int32_t rank_lo_w = T[lo_w].rank;
+        // items a of W_u, matches k of W_w ranked after a: centred at u
+        for (int32_t a = lo_u; a < r; a++) {
+            const TEnt ea = T[a];
+            const uint32_t x = node_of(ea.nbr);
+            if (x == w) continue;
+            PairCounts c;
+            if (!pair_counts(g, pair_key(w, x), rank_lo_w, e.rank, ea.rank, c)) continue;
+            const int32_t from_x = x < w ? c.fa : c.na - c.fa;  // e_k = x -> w: o w.r.t. x
+            const int32_t cnt = c.na;
+            const int di = dir_of(ea.nbr);
+            if (di) {
+                if (dj) { acc[IX(1, 1, 0)] += from_x; acc[IX(1, 1, 1)] += cnt - from_x; }
+                else { acc[IX(1, 0, 0)] += from_x; acc[IX(1, 0, 1)] += cnt - from_x; }
+            } else {
+                if (dj) { acc[IX(0, 1, 0)] += from_x; acc[IX(0, 1, 1)] += cnt - from_x; }
+                else { acc[IX(0, 0, 0)] += from_x; acc[IX(0, 0, 1)] += cnt - from_x; }
+            }
+        }
     }
-    // type II lives at Tri cells 8..15 (T = 1)
-    block_flush<8>(acc, 32 + 8, cells);
+    block_flush<8, 0>(acc, 32 + 8, cells);
 }
 
 __global__ void k_fill_tri_types(unsigned long long *cells) {
@@ -358,7 +523,13 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     }
     {
         PhaseTimer pt(TM_PH_TRI, s);
-        TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
+        if (begin == 0 && end == 2 * g.m) {
+            // whole graph: each edge once, at its source entry
+            TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
+        } else {
+            TM_LAUNCH(k_tri_centre, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end,
+                      dev_cells);
+        }
     }
 }
 

@@ -127,134 +127,152 @@ namespace {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RADIX = 256;
+constexpr int RADIX = 256;  // 8-bit digits; one thread per digit in the tile scan
 
-// Items per thread: a tile (keys + values staged in shared memory) stays
-// under the 48 KB static shared-memory limit.
-template <typename K>
-struct RsTile {
-    static constexpr int ITEMS = sizeof(K) == 4 ? 16 : 8;
+// Items per lane: a warp ranks 32 * ITEMS consecutive items. Wide key/value
+// pairs use half the items to keep registers (one block of 256 threads needs
+// them for the keys, values and ranks of its tile) and shared memory down.
+template <typename K, typename V>
+struct RsCfg {
+    static constexpr int ITEMS = sizeof(K) + sizeof(V) <= 8 ? 16 : 8;
     static constexpr int TILE = RS_THREADS * ITEMS;
 };
 
 template <typename K>
-__global__ void k_radix_hist(const K *__restrict__ keys, int64_t n, int shift,
-                             int32_t *__restrict__ hist, int64_t ntiles) {
-    constexpr int RS_ITEMS = RsTile<K>::ITEMS, RS_TILE = RsTile<K>::TILE;
-    __shared__ int h[RADIX];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-#pragma unroll 4
-    for (int r = 0; r < RS_ITEMS; r++) {
-        int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & (RADIX - 1)], 1);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+__device__ __forceinline__ int digit_of(K k, int shift) {
+    return (int)((unsigned)(k >> shift) & (RADIX - 1));
 }
 
-template <typename K>
+// Per-tile digit histogram (warp-private counters, summed at the end).
+template <typename K, int RS_ITEMS>
 __global__ void __launch_bounds__(RS_THREADS)
-    k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                    K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
-                    int shift, const int32_t *__restrict__ base_off, int64_t ntiles) {
-    constexpr int RS_ITEMS = RsTile<K>::ITEMS, RS_TILE = RsTile<K>::TILE;
-    __shared__ K sk[RS_TILE];
-    __shared__ uint32_t sv[RS_TILE];
-    __shared__ int digit_start[RADIX];  // tile-local exclusive start of each digit
-    __shared__ int running[RADIX];      // items of each digit placed so far
-    __shared__ int warp_cnt[RS_WARPS][RADIX];
+    k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ hist,
+                 int64_t ntiles) {
+    constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+    __shared__ int h[RS_WARPS][RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * 32 * RS_ITEMS;
+#pragma unroll 4
+    for (int r = 0; r < RS_ITEMS; r++) {
+        const int64_t i = wbase + r * 32 + lane;
+        const int d = i < n ? digit_of(keys[i], shift) : RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < RADIX && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; w++) c += h[w][threadIdx.x];
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
+}
+
+// Stable scatter of one tile. Warp w ranks its 512 consecutive items in
+// order with warp-private digit counters; one block-wide scan turns the
+// counters into tile offsets; the tile is reordered in shared memory and
+// written out so that each digit's run goes to consecutive addresses.
+template <typename K, typename V>
+__global__ void __launch_bounds__(RS_THREADS)
+    k_radix_scatter(const K *__restrict__ keys_in, const V *__restrict__ vals_in,
+                    K *__restrict__ keys_out, V *__restrict__ vals_out, int64_t n, int shift,
+                    const int32_t *__restrict__ base_off, int64_t ntiles) {
+    constexpr int RS_ITEMS = RsCfg<K, V>::ITEMS, RS_TILE = RsCfg<K, V>::TILE;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *cnt = reinterpret_cast<int *>(smem);                       // [RS_WARPS][RADIX]
+    K *sk = reinterpret_cast<K *>(cnt + RS_WARPS * RADIX);          // [RS_TILE]
+    V *sv = reinterpret_cast<V *>(sk + RS_TILE);                    // [RS_TILE]
+    __shared__ int digit_off[RADIX];
     __shared__ int gbase[RADIX];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    const int tile_n = (int)(n - base < RS_TILE ? n - base : RS_TILE);
-
-    // tile histogram -> digit_start
-    running[tid] = 0;
-    for (int w = 0; w < RS_WARPS; w++) warp_cnt[w][tid] = 0;
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int tile_n = (int)(n - tbase < RS_TILE ? n - tbase : RS_TILE);
+    for (int i = tid; i < RS_WARPS * RADIX; i += RS_THREADS) cnt[i] = 0;
     __syncthreads();
+
+    K key[RS_ITEMS];
+    V val[RS_ITEMS];
+    int rnk[RS_ITEMS];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int wofs = warp * 32 * RS_ITEMS;
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
-        int li = r * RS_THREADS + tid;
-        if (li < tile_n) atomicAdd(&running[(unsigned)(keys_in[base + li] >> shift) & (RADIX - 1)], 1);
+        const int li = wofs + r * 32 + lane;
+        const bool valid = li < tile_n;
+        key[r] = valid ? keys_in[tbase + li] : K(0);
+        val[r] = valid ? vals_in[tbase + li] : V(0);
+        const int d = valid ? digit_of(key[r], shift) : RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int before = d < RADIX ? cnt[warp * RADIX + d] : 0;
+        __syncwarp();
+        if (d < RADIX && lane == __ffs(peers) - 1) cnt[warp * RADIX + d] = before + __popc(peers);
+        __syncwarp();
+        rnk[r] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
     {
+        // digit `tid`: exclusive prefix over the warps, then over the digits
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) {
+            const int c = cnt[w * RADIX + tid];
+            cnt[w * RADIX + tid] = tot;
+            tot += c;
+        }
         __shared__ int total;
-        int c = running[tid];
-        int ex = block_excl_scan<RS_THREADS>(c, &total);
-        digit_start[tid] = ex;
-        running[tid] = 0;
+        const int ex = block_excl_scan<RS_THREADS>(tot, &total);
+        digit_off[tid] = ex;
         gbase[tid] = base_off[(int64_t)tid * ntiles + blockIdx.x];
     }
     __syncthreads();
-
-    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
-        int li = r * RS_THREADS + tid;
-        bool valid = li < tile_n;
-        K key = valid ? keys_in[base + li] : K(0);
-        uint32_t val = valid ? vals_in[base + li] : 0u;
-        int d = valid ? (int)((unsigned)(key >> shift) & (RADIX - 1)) : RADIX;  // RADIX: no digit
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int lrank = __popc(peers & lt_mask);
-        int leader = __ffs(peers) - 1;
-        if (valid && lane == leader) warp_cnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            // digit tid: prefix over the warps of this round
-            int run = running[tid];
-            for (int w = 0; w < RS_WARPS; w++) {
-                int c = warp_cnt[w][tid];
-                warp_cnt[w][tid] = run;
-                run += c;
-            }
-            running[tid] = run;
-        }
-        __syncthreads();
-        if (valid) {
-            int pos = digit_start[d] + warp_cnt[warp][d] + lrank;
-            sk[pos] = key;
-            sv[pos] = val;
-        }
-        __syncthreads();
-        for (int w = 0; w < RS_WARPS; w++) warp_cnt[w][tid] = 0;
-        __syncthreads();
-    }
-    // write out: consecutive smem positions of one digit go to consecutive
-    // global positions
-    for (int r = 0; r < RS_ITEMS; r++) {
-        int li = r * RS_THREADS + tid;
+        const int li = wofs + r * 32 + lane;
         if (li < tile_n) {
-            K key = sk[li];
-            int d = (int)((unsigned)(key >> shift) & (RADIX - 1));
-            int64_t g = (int64_t)gbase[d] + (li - digit_start[d]);
-            keys_out[g] = key;
-            vals_out[g] = sv[li];
+            const int d = digit_of(key[r], shift);
+            const int pos = digit_off[d] + cnt[warp * RADIX + d] + rnk[r];
+            sk[pos] = key[r];
+            sv[pos] = val[r];
         }
+    }
+    __syncthreads();
+    for (int li = tid; li < tile_n; li += RS_THREADS) {
+        const K k = sk[li];
+        const int d = digit_of(k, shift);
+        const int64_t g = (int64_t)gbase[d] + (li - digit_off[d]);
+        keys_out[g] = k;
+        vals_out[g] = sv[li];
     }
 }
 
-template <typename K>
-void radix_sort_impl(K *keys, uint32_t *vals, K *keys_tmp, uint32_t *vals_tmp, int64_t n,
-                     int bits, cudaStream_t s, K **keys_out, uint32_t **vals_out) {
+template <typename K, typename V>
+void radix_sort_impl(K *keys, V *vals, K *keys_tmp, V *vals_tmp, int64_t n, int bits,
+                     cudaStream_t s, K **keys_out, V **vals_out) {
     K *kin = keys, *kout = keys_tmp;
-    uint32_t *vin = vals, *vout = vals_tmp;
+    V *vin = vals, *vout = vals_tmp;
     if (n > 1 && bits > 0) {
-        constexpr int RS_TILE = RsTile<K>::TILE;
+        constexpr int RS_TILE = RsCfg<K, V>::TILE;
         const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+        const size_t smem = sizeof(int) * RS_WARPS * RADIX + (sizeof(K) + sizeof(V)) * RS_TILE;
+        static bool attr_set = false;
+        if (!attr_set) {
+            TM_CUDA(cudaFuncSetAttribute(k_radix_scatter<K, V>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
         int32_t *hist = dev_alloc_n<int32_t>(RADIX * ntiles + 1, s);
         for (int shift = 0; shift < bits; shift += 8) {
-            TM_LAUNCH(k_radix_hist<K>, (unsigned)ntiles, RS_THREADS, 0, s, kin, n, shift, hist,
+            TM_LAUNCH((k_radix_hist<K, RsCfg<K, V>::ITEMS>), (unsigned)ntiles, RS_THREADS, 0, s, kin, n, shift, hist,
                       ntiles);
             exclusive_scan_i32(hist, hist, RADIX * ntiles, s);
-            TM_LAUNCH(k_radix_scatter<K>, (unsigned)ntiles, RS_THREADS, 0, s, kin, vin, kout,
-                      vout, n, shift, hist, ntiles);
+            TM_LAUNCH((k_radix_scatter<K, V>), (unsigned)ntiles, RS_THREADS, smem, s, kin, vin,
+                      kout, vout, n, shift, hist, ntiles);
             K *tk = kin;
             kin = kout;
             kout = tk;
-            uint32_t *tv = vin;
+            V *tv = vin;
             vin = vout;
             vout = tv;
         }
@@ -269,13 +287,29 @@ void radix_sort_impl(K *keys, uint32_t *vals, K *keys_tmp, uint32_t *vals_tmp, i
 void radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp,
                     int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
                     uint32_t **vals_out) {
-    radix_sort_impl<uint32_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out, vals_out);
+    radix_sort_impl<uint32_t, uint32_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                        vals_out);
 }
 
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
                     int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
                     uint32_t **vals_out) {
-    radix_sort_impl<uint64_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out, vals_out);
+    radix_sort_impl<uint64_t, uint32_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                        vals_out);
+}
+
+void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
+                        uint64_t **vals_out) {
+    radix_sort_impl<uint32_t, uint64_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                        vals_out);
+}
+
+void radix_sort_u64_v64(uint64_t *keys, uint64_t *vals, uint64_t *keys_tmp, uint64_t *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
+                        uint64_t **vals_out) {
+    radix_sort_impl<uint64_t, uint64_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                        vals_out);
 }
 
 }  // namespace tmi

@@ -78,6 +78,8 @@ struct TEnt {
 static_assert(sizeof(TEnt) == 32, "TEnt must be 32 bytes");
 
 // Hash slot: unordered node pair -> its edge list E_(v,w) in the pair list.
+// A pair with a single edge keeps that edge in the slot itself:
+// begin = -(rank + 1), end = 1 if its source is the smaller id, else 0.
 struct PairSlot {
     uint64_t key;  // (smaller id) << 32 | larger id; EMPTY_KEY if unused
     int32_t begin;
@@ -93,8 +95,10 @@ struct DevGraph {
     int32_t *off = nullptr;     // n+1: S_u = T[off[u], off[u+1])
     int32_t *pos_src = nullptr; // m, by rank: T position of the edge at its source
     int32_t *pos_dst = nullptr; // m, by rank: T position at its destination
-    int32_t *pl_rank = nullptr; // m: pair list, grouped by node pair, ranks ascending
-    int32_t *pl_cum = nullptr;  // m+1: exclusive prefix of (src is the smaller id)
+    // pair list, m+1 entries: runs = E_(v,w) (grouped by node pair, ranks
+    // ascending); .x = rank of the edge, .y = exclusive prefix over the list of
+    // "source is the smaller id" (entry m holds the total).
+    int2 *pl = nullptr;
     PairSlot *hash = nullptr;   // open addressing, linear probing
     uint32_t hash_mask = 0;
 };
@@ -114,8 +118,8 @@ __host__ __device__ inline uint32_t hash_pair(uint64_t k) {
 
 // ------------------------------------------------------- primitives
 
-// Exclusive prefix sum: out[i] = sum(in[0..i)), out[n] = total. out may alias in
-// only if it is a different array; n >= 0.
+// Exclusive prefix sum: out[i] = sum(in[0..i)), out[n] = total (out has n+1
+// elements; out == in is allowed when in also has n+1 elements); n >= 0.
 void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
@@ -128,6 +132,12 @@ void radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
                     int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
                     uint32_t **vals_out);
+void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
+                        uint64_t **vals_out);
+void radix_sort_u64_v64(uint64_t *keys, uint64_t *vals, uint64_t *keys_tmp, uint64_t *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
+                        uint64_t **vals_out);
 
 // --------------------------------------------------------- counting
 
