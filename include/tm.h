@@ -154,6 +154,33 @@ enum {
 void tm_profile_enable(int on);
 int tm_profile_read(double ms[], uint64_t calls[]);
 
+/*
+ * tm_count_noalloc - counting for callers that cannot allocate. (The paper
+ * has no counterpart: this is a deployment entry point of this library.)
+ *
+ * A serving thread that must stay inside a device-memory budget fixed up
+ * front, a process whose allocator is sized and locked, or code that must not
+ * risk the implicit synchronisation of cudaMalloc / cudaFree can call this
+ * instead of tm_count. It counts the k graphs gs[i] (built earlier with
+ * tm_build) for windows deltas[i] and writes out[i*36 .. i*36+36) (host
+ * memory, layout as tm_count). It calls no cudaMalloc, cudaFree or other
+ * allocating routine: the 56 counter cells of each graph live in a
+ * file-scope device array of TM_NOALLOC_MAX_GRAPHS * 56 uint64 (112 KiB),
+ * which every device that loads this library holds until the process exits.
+ *   - k must be in [0, TM_NOALLOC_MAX_GRAPHS]; larger k returns TM_EINVAL.
+ *   - The work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream); the call returns after the results are on the host.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call uses the same array and clears the slots it uses first;
+ *     calls whose work overlaps on the GPU (other host threads, other
+ *     streams) race on it and must be serialised by the caller.
+ */
+#define TM_NOALLOC_MAX_GRAPHS 256
+int tm_count_noalloc(const tm_graph *const *gs, const int64_t *deltas, int32_t k, void *stream,
+                     uint64_t *out);
+
 /* Message of the last failed call on this host thread; *code (if not NULL)
  * receives its TM_E* code. Never NULL. */
 const char *tm_last_error(int *code);

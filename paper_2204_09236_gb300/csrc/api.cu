@@ -178,6 +178,17 @@ struct tm_graph {
 
 using namespace tmi;
 
+bool tmi::graph_view(const tm_graph *h, const DevGraph **g, int *device) {
+    if (!h) return false;
+    *g = &h->g;
+    *device = h->device;
+    return true;
+}
+
+void tmi::record_error(int code, const std::string &msg) { set_error(code, msg); }
+
+int tmi::current_device_id() { return current_device(); }
+
 namespace {
 
 tm_graph *build_on(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t m,

@@ -152,4 +152,15 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
                   unsigned long long *dev_cells, cudaStream_t s);
 void launch_fill_tri_types(unsigned long long *dev_cells, cudaStream_t s);
 
+// The whole-graph count (Star/Pair, Tri, type-I/III fill) into dev_cells with
+// no phase timers and no allocation of any kind.
+void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,
+                          cudaStream_t s);
+
+// Read access to a built graph, and error recording, for entry points that
+// live outside api.cu.
+bool graph_view(const tm_graph *h, const DevGraph **g, int *device);
+void record_error(int code, const std::string &msg);
+int current_device_id();
+
 }  // namespace tmi

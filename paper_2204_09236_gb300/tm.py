@@ -41,6 +41,7 @@ _lib.tm_graph_nodes.argtypes = [_P]
 _lib.tm_graph_edges.restype = _i64
 _lib.tm_graph_edges.argtypes = [_P]
 _lib.tm_launch_count.restype = ctypes.c_uint64
+_lib.tm_count_noalloc.argtypes = [_P, _P, ctypes.c_int32, _P, _P]
 _lib.tm_profile_enable.argtypes = [ctypes.c_int]
 _lib.tm_profile_read.argtypes = [_P, _P]
 _lib.tm_last_error.restype = ctypes.c_char_p
@@ -186,6 +187,23 @@ def tm_count_centres(g, delta, centres):
     return split_cells(cells)
 
 
+NOALLOC_MAX_GRAPHS = 256
+
+
+def tm_count_noalloc(graphs, deltas, stream=None):
+    """Counts several built graphs without allocating any memory
+    (tm_count_noalloc); returns a (k, 6, 6) uint64 array."""
+    k = len(graphs)
+    hs = (ctypes.c_void_p * max(k, 1))(*[g.handle for g in graphs])
+    d = np.ascontiguousarray(deltas, np.int64)
+    if len(d) != k:
+        raise ValueError("one delta per graph")
+    out = np.zeros((max(k, 1), 36), np.uint64)
+    _check(_lib.tm_count_noalloc(ctypes.cast(hs, _P), d.ctypes.data_as(_P), k,
+                                 _stream_handle(stream), out.ctypes.data_as(_P)))
+    return out[:k].reshape(k, 6, 6)
+
+
 def split_cells(cells):
     cells = np.asarray(cells, np.uint64).reshape(56)
     return cells[:24].reshape(3, 2, 2, 2), cells[24:32].reshape(2, 2, 2), cells[32:].reshape(3, 2, 2, 2)
@@ -233,6 +251,7 @@ count = tm_count
 count_raw = tm_count_raw
 count_async = tm_count_async
 count_centres = tm_count_centres
+count_noalloc = tm_count_noalloc
 merge = tm_merge
 layout = tm_layout
 launch_count = tm_launch_count
