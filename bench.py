@@ -47,7 +47,105 @@ WORKLOADS = {
                      "10% exact ties", delta=3600),
     "tiny": dict(desc="tiny: 1,000 nodes, 20,000 edges, Zipf(2.1), 20% bursts, 1e6 s",
                  delta=3600),
+    "batch": dict(desc="batch: 512 graphs, m ~ LogNormal(ln 1e5, 1.2) clipped to [1e3, 5e6], "
+                       "N = m/12, Zipf(2.1), 1e6 s, per-graph delta in {60, 600, 3600, 86400}",
+                  delta=None),
 }
+
+
+def gen_batch(scale, seed_offset):
+    cache = os.path.join(tempfile.gettempdir(), f"tm_bench_batch_{scale}_{seed_offset}.npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        m = z["m"]
+        offs = np.concatenate([[0], np.cumsum(m)])
+        graphs = [(z["s"][offs[i]:offs[i + 1]], z["d"][offs[i]:offs[i + 1]],
+                   z["t"][offs[i]:offs[i + 1]]) for i in range(len(m))]
+        return graphs, z["deltas"]
+    graphs, deltas = synth.batch(seed=synth.SEED_BASE + 4 + seed_offset, scale=scale)
+    try:
+        np.savez(cache, s=np.concatenate([g[0] for g in graphs]),
+                 d=np.concatenate([g[1] for g in graphs]), t=np.concatenate([g[2] for g in graphs]),
+                 m=np.array([len(g[0]) for g in graphs]), deltas=np.asarray(deltas))
+    except OSError:
+        pass
+    return graphs, deltas
+
+
+def run_batch(args, rank, world, dist):
+    """Many graphs in one persistent launch vs one graph per launch."""
+    import torch
+    from paper_2204_09236_gb300 import tm
+    graphs, deltas = gen_batch(args.scale, rank)
+    deltas = [int(x) for x in deltas]
+    ms = np.array([len(g[0]) for g in graphs], np.int64)
+    M = int(ms.sum())
+    offs = np.concatenate([[0], np.cumsum(ms)])
+    s_all = torch.from_numpy(np.concatenate([g[0] for g in graphs])).cuda()
+    d_all = torch.from_numpy(np.concatenate([g[1] for g in graphs])).cuda()
+    t_all = torch.from_numpy(np.concatenate([g[2] for g in graphs])).cuda()
+    views = [(s_all[offs[i]:offs[i + 1]], d_all[offs[i]:offs[i + 1]], t_all[offs[i]:offs[i + 1]])
+             for i in range(len(graphs))]
+    torch.cuda.synchronize()
+
+    def batched():
+        g = tm.build_many(views)
+        out = tm.count_many(g, deltas)
+        g.free()
+        return out
+
+    def plain():
+        outs = []
+        for v, dl in zip(views, deltas):
+            g = tm.build(*v)
+            outs.append(tm.count(g, dl))
+            g.free()
+        return np.stack(outs)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            out = fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        st = time.perf_counter()
+        for _ in range(steps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - st) / steps, out
+
+    tune = None
+    if args.tune:
+        g = tm.build_many(views)
+        ie, bps, tms = tm.tune_batch(g, deltas, reps=2)
+        g.free()
+        tune = {"item_entries": ie, "blocks_per_sm": bps, "count_ms": tms}
+    l0 = tm.launch_count()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        step, out_b = timed(batched, args.steps, args.warmup)
+    launches = tm.launch_count() - l0
+    # count only, the graph resident
+    g = tm.build_many(views)
+    c_step, _ = timed(lambda: tm.count_many(g, deltas), args.steps, 1)
+    g.free()
+    p_step, out_p = timed(plain, max(1, args.steps // 2), 1)
+    same = bool((out_b == out_p).all())
+    if dist:
+        x = torch.tensor([step, p_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        step, p_step = float(x[0]), float(x[1])
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * M / step, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded generators standing in for the paper's SNAP datasets)",
+            "config": {"workload": WORKLOADS["batch"]["desc"], "graphs": len(graphs), "m_total": M,
+                       "scale": args.scale, "timing": "wall clock around synchronous calls"},
+            "count_only": {"value": M / c_step, "unit": UNIT, "ms": c_step * 1e3},
+            "plain_one_graph_per_launch": {"value": M / p_step, "unit": UNIT, "ms": p_step * 1e3},
+            "batched_equals_plain": same, "tune": tune, "clocks": clk.summary(),
+            "gpu_launches": launches, "batch_config": tm.batch_get_config()}))
 
 
 def gen(workload, scale, seed_offset):
@@ -195,6 +293,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-count-only", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="batch workload: run the autotuner first")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -211,6 +310,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2204_09236_gb300 import tm
+
+    if args.workload == "batch":
+        run_batch(args, rank, world, dist)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     wl = WORKLOADS[args.workload]
     delta = args.delta if args.delta is not None else wl["delta"]

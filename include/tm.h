@@ -127,6 +127,52 @@ int tm_merge(const uint64_t cells[56], uint64_t out[36]);
  * "12 13 21". Returns TM_OK. */
 int tm_layout(char codes[36][16]);
 
+/*
+ * Batched counting. Many graphs, each with its own window, are counted by
+ * ONE persistent kernel launch fed by a device work queue: each graph's
+ * incident entries are cut into work items (ranges of at most
+ * item_entries entries, for the Star/Pair sweep and for the Tri join), the
+ * items are queued largest first, and every block of the launch takes the
+ * next item with one atomic until the queue is empty (the paper's dynamic
+ * scheduling over centres, Sec. IV-C, as a device queue). The launch
+ * sequence (job table and queue uploads, clears, the kernel, the Tri type
+ * fill, the cell download) is captured once in a CUDA graph and replayed;
+ * only the staged job table and queue change between calls. Synchronous.
+ */
+
+/* Counts gs[i] with window deltas[i] for i < n; out[i*36 .. i*36+36) as in
+ * tm_count (host memory). All graphs must be on the current device. */
+int tm_count_batch(const tm_graph *const *gs, const int64_t *deltas, int32_t n, uint64_t *out);
+
+/* Builds k graphs as ONE device graph of k components (graph c's node v
+ * becomes node base_c + v; its edge ids keep their order), so that all k are
+ * sorted and indexed by one pass of the build instead of k small ones.
+ * src[c], dst[c], t[c]: arrays of graph c (host or device memory, m[c]
+ * entries, same rules as tm_build). Counting the whole result with tm_count
+ * gives the sum over the components; tm_count_many counts each component
+ * with its own window. Returns NULL on error (as tm_build). */
+tm_graph *tm_build_many(int32_t k, const int32_t *const *src, const int32_t *const *dst,
+                        const int64_t *const *t, const int64_t *m);
+
+/* Number of components (1 for a graph from tm_build; -1 for NULL). */
+int32_t tm_graph_components(const tm_graph *g);
+
+/* Counts each component c of g (tm_build_many) with window deltas[c] in one
+ * batched launch; out[c*36 .. c*36+36) as in tm_count. */
+int tm_count_many(const tm_graph *g, const int64_t *deltas, uint64_t *out);
+
+/* Batching parameters: entries per work item (>= 256; 0 keeps the current
+ * value) and blocks per SM of the persistent launch (0 = as many as fit). */
+int tm_batch_config(int64_t item_entries, int32_t blocks_per_sm);
+int tm_batch_get_config(int64_t *item_entries, int32_t *blocks_per_sm);
+
+/* Autotuner: times tm_count_many on g with windows deltas (reps timed runs
+ * per setting) over item sizes {4096, 16384, 65536, 262144} and blocks per
+ * SM {1, 2, 4, ..., max}, checks that every setting gives the same cells,
+ * makes the fastest the library's setting and reports it. */
+int tm_tune_batch(const tm_graph *g, const int64_t *deltas, int32_t reps,
+                  int64_t *best_item_entries, int32_t *best_blocks_per_sm, double *best_ms);
+
 /* Number of nodes / edges of a built graph (-1 for NULL). */
 int64_t tm_graph_nodes(const tm_graph *g);
 int64_t tm_graph_edges(const tm_graph *g);

@@ -171,11 +171,6 @@ int guarded(F &&f) {
 }  // namespace
 }  // namespace tmi
 
-struct tm_graph {
-    tmi::DevGraph g;
-    int device;
-};
-
 using namespace tmi;
 
 bool tmi::graph_view(const tm_graph *h, const DevGraph **g, int *device) {

@@ -237,20 +237,30 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
     }
 }
 
+// Star/Pair contributions of the entries [begin, end) of g.T, visited by
+// threads tid, tid + nthreads, ...
+__device__ __forceinline__ void star_pair_range(const TEnt *__restrict__ T,
+                                                const int32_t *__restrict__ off, int64_t m,
+                                                int64_t delta, int64_t begin, int64_t end,
+                                                int64_t tid, int64_t nthreads,
+                                                unsigned long long (&acc)[32]) {
+    const int64_t m2 = 2 * m;
+    for (int64_t i = begin + tid; i < end; i += nthreads) {
+        const int32_t r = (int32_t)i;
+        const TEnt e = T[r];
+        if (dir_of(e.nbr)) star_pair_entry<1>(T, off, m2, m, delta, r, e, acc);
+        else star_pair_entry<0>(T, off, m2, m, delta, r, e, acc);
+    }
+}
+
 __global__ void __launch_bounds__(THREADS)
     k_star_pair(const TEnt *__restrict__ T, const int32_t *__restrict__ off, int64_t m, int64_t delta,
                 int32_t begin, int32_t end, unsigned long long *__restrict__ cells) {
     unsigned long long acc[32];
 #pragma unroll
     for (int c = 0; c < 32; c++) acc[c] = 0;
-    const int64_t m2 = 2 * m;
-    for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = (int32_t)i;
-        const TEnt e = T[r];
-        if (dir_of(e.nbr)) star_pair_entry<1>(T, off, m2, m, delta, r, e, acc);
-        else star_pair_entry<0>(T, off, m2, m, delta, r, e, acc);
-    }
+    star_pair_range(T, off, m, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                    (int64_t)gridDim.x * blockDim.x, acc);
     // acc order: Pair, Star-I, Star-II, Star-III -> cells Star[T] at 0.., Pair at 24..
     block_flush<24, 8>(acc, 0, cells);
     block_flush<8, 0>(acc, 24, cells);
@@ -384,19 +394,16 @@ constexpr int TRI_WARPS = THREADS / 32;
 // neighbour node counts both. The probes of the 32 edges of a warp are
 // flattened into one list that all lanes share, so a lane never waits for
 // another lane's long window.
-__global__ void __launch_bounds__(THREADS)
-    k_tri(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-          unsigned long long *__restrict__ cells) {
-    __shared__ TriEdge edges[TRI_WARPS][32];
-    __shared__ int32_t incl[TRI_WARPS][32];
-    unsigned long long acc[8];
-#pragma unroll
-    for (int c = 0; c < 8; c++) acc[c] = 0;
+// Tri joins of the edges whose source entries lie in [begin, end) of g.T,
+// visited 32 entries at a time by warps wid, wid + nwarps, ...; `edges` and
+// `incl` are the calling warp's shared-memory staging (32 slots each).
+__device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int64_t begin,
+                                          int64_t end, int64_t wid, int64_t nwarps,
+                                          TriEdge *edges, int32_t *incl,
+                                          unsigned long long (&acc)[8]) {
     const TEnt *__restrict__ T = g.T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = begin + blockIdx.x * (int64_t)blockDim.x + warp * 32; base < end;
-         base += stride) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = begin + wid * 32; base < end; base += nwarps * 32) {
         const int64_t r = base + lane;
         TriEdge E;
         E.work = 0;
@@ -427,8 +434,8 @@ __global__ void __launch_bounds__(THREADS)
         const int32_t inc = warp_incl_scan_i32(E.work);
         const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
         if (total == 0) continue;
-        edges[warp][lane] = E;
-        incl[warp][lane] = inc;
+        edges[lane] = E;
+        incl[lane] = inc;
         __syncwarp();
         for (int32_t jb = 0; jb < total; jb += 32) {
             const int32_t j = jb + lane;
@@ -437,16 +444,36 @@ __global__ void __launch_bounds__(THREADS)
                 int lo = 0, hi = 31;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (incl[warp][mid] > j) hi = mid;
+                    if (incl[mid] > j) hi = mid;
                     else lo = mid + 1;
                 }
-                const TriEdge &B = edges[warp][lo];
-                const int32_t k = j - (incl[warp][lo] - B.work);
+                const TriEdge &B = edges[lo];
+                const int32_t k = j - (incl[lo] - B.work);
                 tri_probe(g, B, T[B.small_lo + k], acc);
             }
         }
         __syncwarp();
     }
+}
+
+// Walks S_u entries in order; each edge is taken once, at its source entry
+// (direction o). Each edge e_j = (u -> w) is the later centre edge of the
+// type-II triangles at u and at w, whose other centre edges lie in the
+// windows W_u(e_j) and W_w(e_j), so one join of the two windows on the
+// neighbour node counts both. The probes of the 32 edges of a warp are
+// flattened into one list that all lanes share, so a lane never waits for
+// another lane's long window.
+__global__ void __launch_bounds__(THREADS)
+    k_tri(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
+          unsigned long long *__restrict__ cells) {
+    __shared__ TriEdge edges[TRI_WARPS][32];
+    __shared__ int32_t incl[TRI_WARPS][32];
+    unsigned long long acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0;
+    const int warp = threadIdx.x >> 5;
+    tri_range(g, delta, begin, end, blockIdx.x * (int64_t)TRI_WARPS + warp,
+              (int64_t)gridDim.x * TRI_WARPS, edges[warp], incl[warp], acc);
     // type II lives at Tri cells 8..15 (T = 1)
     block_flush<8, 0>(acc, 32 + 8, cells);
 }
@@ -507,7 +534,76 @@ __global__ void k_fill_tri_types(unsigned long long *cells) {
             }
 }
 
+// The persistent batched count: every block repeatedly takes the next work
+// item (a range of one job's entries, largest items first) with one atomic
+// on the queue head, sweeps it with the same device functions as the
+// one-graph kernels, and adds its block total into that job's cells. The
+// queue is fixed for the launch, so no block ever waits for another.
+__global__ void __launch_bounds__(THREADS)
+    k_batch(const BatchJob *__restrict__ jobs, const WorkItem *__restrict__ items,
+            const int32_t *__restrict__ nitems_ptr, int32_t *__restrict__ head) {
+    __shared__ TriEdge edges[TRI_WARPS][32];
+    __shared__ int32_t incl[TRI_WARPS][32];
+    __shared__ int32_t cur;
+    const int32_t nitems = *nitems_ptr;
+    const int warp = threadIdx.x >> 5;
+    while (true) {
+        __syncthreads();  // the previous item's reads of `cur` are done
+        if (threadIdx.x == 0) cur = atomicAdd(head, 1);
+        __syncthreads();
+        const int32_t i = cur;
+        if (i >= nitems) break;
+        const WorkItem it = items[i];
+        const DevGraph g = jobs[it.job].g;
+        const int64_t delta = jobs[it.job].delta;
+        unsigned long long *cells = jobs[it.job].cells;
+        if (it.kind == 0) {
+            unsigned long long acc[32];
+#pragma unroll
+            for (int c = 0; c < 32; c++) acc[c] = 0;
+            star_pair_range(g.T, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x, acc);
+            block_flush<24, 8>(acc, 0, cells);
+            block_flush<8, 0>(acc, 24, cells);
+        } else {
+            unsigned long long acc[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) acc[c] = 0;
+            tri_range(g, delta, it.begin, it.end, warp, TRI_WARPS, edges[warp], incl[warp], acc);
+            block_flush<8, 0>(acc, 32 + 8, cells);
+        }
+    }
+}
+
+__global__ void k_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *njobs) return;
+    unsigned long long *tri = cells + (size_t)NCELLS * j + 32;
+    for (int di = 0; di < 2; di++)
+        for (int dj = 0; dj < 2; dj++)
+            for (int dk = 0; dk < 2; dk++) {
+                const unsigned long long v = tri[8 + IX(di, dj, dk)];
+                tri[IX(1 - dk, 1 - dj, 1 - di)] = v;  // type I
+                tri[16 + IX(1 - di, dk, dj)] = v;     // type III
+            }
+}
+
 }  // namespace
+
+int batch_blocks_per_sm() {
+    int nb = 0;
+    TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, THREADS, 0));
+    return nb > 0 ? nb : 1;
+}
+
+void launch_batch(const BatchJob *jobs, const WorkItem *items, const int32_t *nitems,
+                  int32_t *head, int grid, cudaStream_t s) {
+    TM_LAUNCH(k_batch, (unsigned)grid, THREADS, 0, s, jobs, items, nitems, head);
+}
+
+void launch_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs, int max_jobs,
+                                 cudaStream_t s) {
+    TM_LAUNCH(k_fill_tri_types_batch, (unsigned)((max_jobs + 127) / 128), 128, 0, s, cells, njobs);
+}
 
 void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
                   unsigned long long *dev_cells, cudaStream_t s) {

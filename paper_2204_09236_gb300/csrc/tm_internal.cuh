@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "tm.h"
 
@@ -157,6 +158,34 @@ void launch_fill_tri_types(unsigned long long *dev_cells, cudaStream_t s);
 void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,
                           cudaStream_t s);
 
+// ---------------------------------------------------------- batching
+
+// One counting job of a batched launch: a graph (or one component of a
+// multi-component graph), its window and its 56 output cells.
+struct BatchJob {
+    DevGraph g;
+    int64_t delta;
+    unsigned long long *cells;
+};
+
+// A contiguous range of one job's incident entries, for the Star/Pair sweep
+// (kind 0) or the Tri join (kind 1).
+struct WorkItem {
+    int32_t job;
+    int32_t kind;
+    int32_t begin;
+    int32_t end;
+};
+
+// One persistent launch: `grid` blocks pop items from `items[0, *nitems)` in
+// order through the counter *head, which must be zero at launch.
+void launch_batch(const BatchJob *jobs, const WorkItem *items, const int32_t *nitems,
+                  int32_t *head, int grid, cudaStream_t s);
+// Type-I/III Tri cells of jobs [0, *njobs) from their type-II cells.
+void launch_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs, int max_jobs,
+                                 cudaStream_t s);
+int batch_blocks_per_sm();
+
 // Read access to a built graph, and error recording, for entry points that
 // live outside api.cu.
 bool graph_view(const tm_graph *h, const DevGraph **g, int *device);
@@ -164,3 +193,11 @@ void record_error(int code, const std::string &msg);
 int current_device_id();
 
 }  // namespace tmi
+
+// The opaque handle of include/tm.h. A graph built from several component
+// graphs (tm_build_many) keeps where each component's entries start in T.
+struct tm_graph {
+    tmi::DevGraph g;
+    int device = 0;
+    std::vector<int32_t> comp_toff;  // k+1 entry offsets; empty: one component
+};

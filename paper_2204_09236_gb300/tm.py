@@ -42,6 +42,15 @@ _lib.tm_graph_edges.restype = _i64
 _lib.tm_graph_edges.argtypes = [_P]
 _lib.tm_launch_count.restype = ctypes.c_uint64
 _lib.tm_count_noalloc.argtypes = [_P, _P, ctypes.c_int32, _P, _P]
+_lib.tm_count_batch.argtypes = [_P, _P, ctypes.c_int32, _P]
+_lib.tm_build_many.restype = _P
+_lib.tm_build_many.argtypes = [ctypes.c_int32, _P, _P, _P, _P]
+_lib.tm_graph_components.restype = ctypes.c_int32
+_lib.tm_graph_components.argtypes = [_P]
+_lib.tm_count_many.argtypes = [_P, _P, _P]
+_lib.tm_batch_config.argtypes = [_i64, ctypes.c_int32]
+_lib.tm_batch_get_config.argtypes = [_P, _P]
+_lib.tm_tune_batch.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P]
 _lib.tm_profile_enable.argtypes = [ctypes.c_int]
 _lib.tm_profile_read.argtypes = [_P, _P]
 _lib.tm_last_error.restype = ctypes.c_char_p
@@ -204,6 +213,81 @@ def tm_count_noalloc(graphs, deltas, stream=None):
     return out[:k].reshape(k, 6, 6)
 
 
+def _handles(graphs):
+    return (ctypes.c_void_p * max(len(graphs), 1))(*[g.handle for g in graphs])
+
+
+def tm_count_batch(graphs, deltas):
+    """One persistent launch over all graphs; returns (n, 6, 6) uint64."""
+    n = len(graphs)
+    d = np.ascontiguousarray(deltas, np.int64)
+    if len(d) != n:
+        raise ValueError("one delta per graph")
+    out = np.zeros((max(n, 1), 36), np.uint64)
+    hs = _handles(graphs)
+    _check(_lib.tm_count_batch(ctypes.cast(hs, _P), d.ctypes.data_as(_P), n,
+                               out.ctypes.data_as(_P)))
+    return out[:n].reshape(n, 6, 6)
+
+
+def tm_build_many(graphs):
+    """One device graph whose components are the given (src, dst, t) graphs."""
+    k = len(graphs)
+    keep, ps, pd, pt, ms = [], [], [], [], []
+    for s_, d_, t_ in graphs:
+        a, ka = _ptr(s_, np.int32)
+        b, kb = _ptr(d_, np.int32)
+        c, kc = _ptr(t_, np.int64)
+        keep += [ka, kb, kc]
+        ps.append(a.value)
+        pd.append(b.value)
+        pt.append(c.value)
+        ms.append(len(ka))
+    arr = lambda v: (ctypes.c_void_p * max(k, 1))(*v)
+    m = np.ascontiguousarray(ms, np.int64)
+    h = _lib.tm_build_many(k, ctypes.cast(arr(ps), _P), ctypes.cast(arr(pd), _P),
+                           ctypes.cast(arr(pt), _P), m.ctypes.data_as(_P))
+    if not h:
+        code, msg = last_error()
+        raise TmError(code, msg)
+    return Graph(h)
+
+
+def tm_graph_components(g):
+    return int(_lib.tm_graph_components(g.handle))
+
+
+def tm_count_many(g, deltas):
+    k = tm_graph_components(g)
+    d = np.ascontiguousarray(deltas, np.int64)
+    if len(d) != k:
+        raise ValueError(f"one delta per component ({k})")
+    out = np.zeros((k, 36), np.uint64)
+    _check(_lib.tm_count_many(g.handle, d.ctypes.data_as(_P), out.ctypes.data_as(_P)))
+    return out.reshape(k, 6, 6)
+
+
+def tm_batch_config(item_entries=0, blocks_per_sm=0):
+    _check(_lib.tm_batch_config(int(item_entries), int(blocks_per_sm)))
+
+
+def tm_batch_get_config():
+    ie = ctypes.c_int64(0)
+    b = ctypes.c_int32(0)
+    _check(_lib.tm_batch_get_config(ctypes.byref(ie), ctypes.byref(b)))
+    return ie.value, b.value
+
+
+def tm_tune_batch(g, deltas, reps=3):
+    d = np.ascontiguousarray(deltas, np.int64)
+    ie = ctypes.c_int64(0)
+    b = ctypes.c_int32(0)
+    ms = ctypes.c_double(0)
+    _check(_lib.tm_tune_batch(g.handle, d.ctypes.data_as(_P), int(reps), ctypes.byref(ie),
+                              ctypes.byref(b), ctypes.byref(ms)))
+    return ie.value, b.value, ms.value
+
+
 def split_cells(cells):
     cells = np.asarray(cells, np.uint64).reshape(56)
     return cells[:24].reshape(3, 2, 2, 2), cells[24:32].reshape(2, 2, 2), cells[32:].reshape(3, 2, 2, 2)
@@ -252,6 +336,13 @@ count_raw = tm_count_raw
 count_async = tm_count_async
 count_centres = tm_count_centres
 count_noalloc = tm_count_noalloc
+count_batch = tm_count_batch
+build_many = tm_build_many
+count_many = tm_count_many
+graph_components = tm_graph_components
+batch_config = tm_batch_config
+batch_get_config = tm_batch_get_config
+tune_batch = tm_tune_batch
 merge = tm_merge
 layout = tm_layout
 launch_count = tm_launch_count
