@@ -173,6 +173,57 @@ int tm_batch_get_config(int64_t *item_entries, int32_t *blocks_per_sm);
 int tm_tune_batch(const tm_graph *g, const int64_t *deltas, int32_t reps,
                   int64_t *best_item_entries, int32_t *best_blocks_per_sm, double *best_ms);
 
+/*
+ * Serving loop. A server keeps built graphs resident on the device for
+ * repeat queries and counts requests as they arrive: worker threads (each
+ * with its own stream) repeatedly take the pending requests that can be
+ * admitted now (continuous batching) - re-queries of resident graphs, and
+ * new graphs whose estimated device bytes fit in the budget after evicting
+ * the least recently used idle graphs - build the new graphs and count the
+ * whole wave in one batched launch (tm_count_batch). A request that arrives
+ * while waves are on the device joins a later wave as slots and memory free
+ * up. Latency = completion minus submission (host clock).
+ */
+typedef struct tm_server tm_server;
+
+typedef struct {
+    int64_t key;          /* caller's key of the graph */
+    const int32_t *src;   /* new graph: host arrays of m edges (copied at */
+    const int32_t *dst;   /*   submission); a re-query of a resident graph */
+    const int64_t *t;     /*   passes NULL and m = 0 */
+    int64_t m;
+    int64_t n_hint;       /* node count if known (memory estimate), else 0 */
+    int64_t delta;        /* window, >= 0 */
+} tm_request_desc;
+
+typedef struct {
+    int64_t submitted, completed, failed, pending;
+    int64_t resident_graphs, resident_bytes, evictions, builds, waves, edges_counted;
+    double p50_ms, p99_ms, max_ms; /* latency quantiles of completed requests */
+} tm_server_stats_t;
+
+/* budget_bytes: device bytes for resident graphs plus builds in progress;
+ * workers: 1..64 worker threads (streams); max_wave: most requests per wave.
+ * NULL on error. */
+tm_server *tm_server_create(int64_t budget_bytes, int32_t workers, int32_t max_wave);
+/* Returns the request id (>= 0) or a negative TM_E* code. A request whose
+ * key names a resident graph counts that graph (its edges, if given, are not
+ * used). */
+int64_t tm_server_submit(tm_server *s, const tm_request_desc *req);
+/* TM_OK with out[36] (as tm_count) and the latency when done, 1 while
+ * pending, or the request's negative error code (TM_EBUDGET: the graph can
+ * never fit the budget; TM_EINVAL: unknown key without edges, bad input). */
+int tm_server_poll(tm_server *s, int64_t id, uint64_t out[36], double *latency_ms);
+/* As tm_server_poll, waiting up to timeout_s seconds; TM_ETIMEOUT if the
+ * request is still pending then. */
+int tm_server_wait(tm_server *s, int64_t id, uint64_t out[36], double *latency_ms,
+                   double timeout_s);
+int tm_server_stats(tm_server *s, tm_server_stats_t *st);
+/* Keys of the resident graphs (up to cap written); returns how many there are. */
+int32_t tm_server_resident(tm_server *s, int64_t *keys, int32_t cap);
+/* Finishes the queued requests, stops the workers, frees every graph. */
+void tm_server_destroy(tm_server *s);
+
 /* Number of nodes / edges of a built graph (-1 for NULL). */
 int64_t tm_graph_nodes(const tm_graph *g);
 int64_t tm_graph_edges(const tm_graph *g);

@@ -274,6 +274,22 @@ __global__ void k_comp_toff(const int32_t *__restrict__ off, const int32_t *__re
 }
 
 }  // namespace
+
+void *new_batch_plan() { return new BatchPlan(); }
+void delete_batch_plan(void *plan) { delete static_cast<BatchPlan *>(plan); }
+
+// Counts whole graphs with their windows on stream s with a caller-owned plan.
+void run_batch_on(const std::vector<const DevGraph *> &graphs, const std::vector<int64_t> &deltas,
+                  void *plan, cudaStream_t s, std::vector<uint64_t> &cells) {
+    std::vector<JobSpec> jobs;
+    for (size_t i = 0; i < graphs.size(); i++)
+        jobs.push_back(JobSpec{graphs[i], deltas[i], 0, (int32_t)(2 * graphs[i]->m)});
+    int64_t ie;
+    int32_t bps;
+    current_config(ie, bps);
+    static_cast<BatchPlan *>(plan)->run(jobs, ie, bps, s, cells);
+}
+
 }  // namespace tmi
 
 using namespace tmi;

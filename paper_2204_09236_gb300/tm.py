@@ -51,6 +51,31 @@ _lib.tm_count_many.argtypes = [_P, _P, _P]
 _lib.tm_batch_config.argtypes = [_i64, ctypes.c_int32]
 _lib.tm_batch_get_config.argtypes = [_P, _P]
 _lib.tm_tune_batch.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P]
+
+
+class _ReqDesc(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_int64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("m", ctypes.c_int64), ("n_hint", ctypes.c_int64),
+                ("delta", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "failed", "pending", "resident_graphs", "resident_bytes",
+        "evictions", "builds", "waves", "edges_counted")] + [
+        ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
+_lib.tm_server_create.restype = _P
+_lib.tm_server_create.argtypes = [_i64, ctypes.c_int32, ctypes.c_int32]
+_lib.tm_server_submit.restype = _i64
+_lib.tm_server_submit.argtypes = [_P, ctypes.POINTER(_ReqDesc)]
+_lib.tm_server_poll.argtypes = [_P, _i64, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.tm_server_wait.argtypes = [_P, _i64, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_double]
+_lib.tm_server_stats.argtypes = [_P, ctypes.POINTER(_Stats)]
+_lib.tm_server_resident.restype = ctypes.c_int32
+_lib.tm_server_resident.argtypes = [_P, _P, ctypes.c_int32]
+_lib.tm_server_destroy.argtypes = [_P]
 _lib.tm_profile_enable.argtypes = [ctypes.c_int]
 _lib.tm_profile_read.argtypes = [_P, _P]
 _lib.tm_last_error.restype = ctypes.c_char_p
@@ -286,6 +311,75 @@ def tm_tune_batch(g, deltas, reps=3):
     _check(_lib.tm_tune_batch(g.handle, d.ctypes.data_as(_P), int(reps), ctypes.byref(ie),
                               ctypes.byref(b), ctypes.byref(ms)))
     return ie.value, b.value, ms.value
+
+
+class Server:
+    """tm_server_*: continuous-batching count server with resident graphs."""
+
+    def __init__(self, budget_bytes, workers=2, max_wave=64):
+        h = _lib.tm_server_create(int(budget_bytes), int(workers), int(max_wave))
+        if not h:
+            code, msg = last_error()
+            raise TmError(code, msg)
+        self._h = h
+
+    def submit(self, key, delta, src=None, dst=None, t=None, n_hint=0):
+        d = _ReqDesc(key=int(key), delta=int(delta), n_hint=int(n_hint))
+        keep = None
+        if src is not None:
+            a = np.ascontiguousarray(src, np.int32)
+            b = np.ascontiguousarray(dst, np.int32)
+            c = np.ascontiguousarray(t, np.int64)
+            keep = (a, b, c)
+            d.src, d.dst, d.t = a.ctypes.data, b.ctypes.data, c.ctypes.data
+            d.m = len(a)
+        rid = _lib.tm_server_submit(self._h, ctypes.byref(d))
+        del keep  # the server copied the edges
+        if rid < 0:
+            code, msg = last_error()
+            raise TmError(int(rid), msg)
+        return int(rid)
+
+    def poll(self, rid):
+        out = np.zeros(36, np.uint64)
+        lat = ctypes.c_double(0)
+        rc = _lib.tm_server_poll(self._h, int(rid), out.ctypes.data_as(_P), ctypes.byref(lat))
+        if rc < 0:
+            code, msg = last_error()
+            raise TmError(rc, msg)
+        return rc, out.reshape(6, 6), lat.value
+
+    def wait(self, rid, timeout=120.0):
+        out = np.zeros(36, np.uint64)
+        lat = ctypes.c_double(0)
+        rc = _lib.tm_server_wait(self._h, int(rid), out.ctypes.data_as(_P), ctypes.byref(lat),
+                                 float(timeout))
+        if rc != 0:
+            code, msg = last_error()
+            raise TmError(rc, msg)
+        return out.reshape(6, 6), lat.value
+
+    def stats(self):
+        st = _Stats()
+        _check(_lib.tm_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+    def resident(self):
+        n = _lib.tm_server_resident(self._h, None, 0)
+        keys = np.zeros(max(n, 1), np.int64)
+        n = _lib.tm_server_resident(self._h, keys.ctypes.data_as(_P), len(keys))
+        return [int(k) for k in keys[:min(n, len(keys))]]
+
+    def close(self):
+        if self._h:
+            _lib.tm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def split_cells(cells):
