@@ -92,15 +92,22 @@ __global__ void k_rank_edges(const K *__restrict__ tkey, const uint64_t *__restr
 }
 
 // Incident entries in rank order, keyed by centre: entry 2i+side of edge rank i
-// is at its source (side 0, direction o) or destination (side 1, direction in).
+// is at its source (side 0, direction o) or destination (side 1, direction in),
+// carrying its timestamp and neighbour through the sort.
 __global__ void k_entry_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
-                             int64_t m, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                             const int64_t *__restrict__ et, int64_t m,
+                             uint32_t *__restrict__ keys, EntryPayload *__restrict__ vals) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * m;
          j += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = j >> 1;
-        int side = (int)(j & 1);
-        keys[j] = (uint32_t)(side ? edst[i] : esrc[i]);
-        vals[j] = (uint32_t)j;  // (rank << 1) | side
+        const int64_t i = j >> 1;
+        const int side = (int)(j & 1);
+        const uint32_t a = (uint32_t)esrc[i], b = (uint32_t)edst[i];
+        keys[j] = side ? b : a;
+        EntryPayload p;
+        p.t = et[i];
+        p.nbr = side ? a : b;
+        p.code = (uint32_t)j;  // (rank << 1) | side
+        vals[j] = p;
     }
 }
 
@@ -115,35 +122,35 @@ __global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64
     }
 }
 
-__global__ void k_dir_flags(const uint32_t *__restrict__ code, int64_t n2, int32_t *__restrict__ f) {
+__global__ void k_dir_flags(const EntryPayload *__restrict__ pl, int64_t n2,
+                            int32_t *__restrict__ f) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x)
-        f[p] = (int32_t)(code[p] & 1u);
+        f[p] = (int32_t)(pl[p].code & 1u);
 }
 
-__global__ void k_fill_T(const uint32_t *__restrict__ centre, const uint32_t *__restrict__ code,
-                         const int32_t *__restrict__ cin, const int32_t *__restrict__ esrc,
-                         const int32_t *__restrict__ edst, const int64_t *__restrict__ et,
-                         int64_t n2, TEnt *__restrict__ T, int32_t *__restrict__ pos_src,
-                         int32_t *__restrict__ pos_dst, int32_t *__restrict__ minflag) {
+__global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload *__restrict__ pl,
+                         const int32_t *__restrict__ cin, int64_t n2, TEnt *__restrict__ T,
+                         int32_t *__restrict__ pos_src, int32_t *__restrict__ pos_dst,
+                         int32_t *__restrict__ minflag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = code[p];
-        int32_t rank = (int32_t)(c >> 1);
-        int side = (int)(c & 1u);
-        const uint32_t nbr = (uint32_t)(side ? esrc[rank] : edst[rank]);
+        const EntryPayload q = pl[p];
+        const int32_t rank = (int32_t)(q.code >> 1);
+        const int side = (int)(q.code & 1u);
+        const uint32_t c = centre[p];
         TEnt e;
-        e.t = et[rank];
-        e.nbr = nbr | ((uint32_t)side << 31);
+        e.t = q.t;
+        e.nbr = q.nbr | ((uint32_t)side << 31);
         e.rank = rank;
         e.cin = cin[p];
         e.prev = -1;
         e.next = -1;
-        e.centre = (int32_t)centre[p];
+        e.centre = (int32_t)c;
         T[p] = e;
         if (side) pos_dst[rank] = (int32_t)p;
         else pos_src[rank] = (int32_t)p;
-        minflag[p] = centre[p] < nbr ? 1 : 0;
+        minflag[p] = c < q.nbr ? 1 : 0;
     }
 }
 
@@ -441,16 +448,19 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     {
         PhaseTimer pt(TM_PH_INCIDENT, s);
         uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
-        uint32_t *v1 = dev_alloc_n<uint32_t>(n2, s), *v2 = dev_alloc_n<uint32_t>(n2, s);
-        TM_LAUNCH(k_entry_keys, grid_for(n2), 256, 0, s, esrc, edst, m, k1, v1);
-        uint32_t *sk, *sv;
-        radix_sort_u32(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
+        EntryPayload *v1 = dev_alloc_n<EntryPayload>(n2, s), *v2 = dev_alloc_n<EntryPayload>(n2, s);
+        TM_LAUNCH(k_entry_keys, grid_for(n2), 256, 0, s, esrc, edst, et, m, k1, v1);
+        dev_free(et, s);
+        et = nullptr;
+        uint32_t *sk;
+        EntryPayload *sv;
+        radix_sort_u32_ent(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
         TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, sk, n2, n, g.off);
         int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
         TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
         exclusive_scan_i32(flags, cin, n2, s);
-        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, esrc, edst, et, n2, g.T,
-                  g.pos_src, g.pos_dst, minflag);
+        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.pos_src, g.pos_dst,
+                  minflag);
         dev_free(flags, s);
         dev_free(cin, s);
         dev_free(k1, s);
@@ -458,7 +468,6 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         dev_free(v1, s);
         dev_free(v2, s);
     }
-    dev_free(et, s);
     dev_free(esrc, s);
     dev_free(edst, s);
 

@@ -126,18 +126,35 @@ __device__ void block_flush(const unsigned long long (&acc)[NA], int cell0,
     if (threadIdx.x < NC && red[threadIdx.x]) atomicAdd(&cells[cell0 + threadIdx.x], red[threadIdx.x]);
 }
 
-// Accumulator index helpers (local arrays with compile-time indices).
-//   acc[0..7]   Pair[d1][d2][d3]
-//   acc[8..15]  Star-I[d1][d2][d3]
-//   acc[16..23] Star-II
-//   acc[24..31] Star-III
+// Star/Pair accumulator layout (shared memory, one set per block):
+//   sacc[0..7]   Pair[d1][d2][d3]
+//   sacc[8..15]  Star-I[d1][d2][d3]
+//   sacc[16..23] Star-II
+//   sacc[24..31] Star-III
+// Most entries contribute nothing (no same-neighbour entry in their window),
+// so contributions go straight to shared memory with atomics instead of
+// living in 32 registers per thread.
 #define IX(a, b, c) ((((a) * 2) + (b)) * 2 + (c))
+
+__device__ __forceinline__ void add_cell(unsigned long long *sacc, int i, uint64_t v) {
+    if (v) atomicAdd(&sacc[i], (unsigned long long)v);
+}
+
+// Block total of sacc[32] into the global cells (Star 0..23, Pair 24..31).
+__device__ __forceinline__ void flush_star_pair(const unsigned long long *sacc,
+                                                unsigned long long *__restrict__ cells) {
+    if (threadIdx.x < 32) {
+        const int i = threadIdx.x;
+        const unsigned long long v = sacc[i];
+        if (v) atomicAdd(&cells[i < 8 ? 24 + i : i - 8], v);
+    }
+}
 
 template <int D3>
 __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
                                                 const int32_t *__restrict__ off, int64_t m2,
                                                 int64_t m, int64_t delta, int32_t r,
-                                                const TEnt &e, unsigned long long (&acc)[32]) {
+                                                const TEnt &e, unsigned long long *sacc) {
     const int64_t tr = e.t;
     const int32_t u = e.centre;
     const int32_t seg_b = off[u], seg_end = off[u + 1];
@@ -194,19 +211,19 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
 #pragma unroll
                 for (int d2 = 0; d2 < 2; d2++) {
                     const uint64_t sp = c2s[d1][d2];
-                    acc[IX(d1, d2, D3)] += sp;                                       // Pair
-                    acc[16 + IX(d1, d2, D3)] += X[d1][d2] - sp;                      // Star-II
-                    const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;  // C_d1(lo)
-                    acc[8 + IX(d1, d2, D3)] += Yp[d2][d1] - n[d2] * base - sp;       // Star-I
-                    acc[24 + IX(d1, d2, D3)] -= sp;                                  // Star-III
+                    add_cell(sacc, IX(d1, d2, D3), sp);                                // Pair
+                    add_cell(sacc, 16 + IX(d1, d2, D3), X[d1][d2] - sp);               // Star-II
+                    const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;    // C_d1(lo)
+                    add_cell(sacc, 8 + IX(d1, d2, D3), Yp[d2][d1] - n[d2] * base - sp); // Star-I
+                    add_cell(sacc, 24 + IX(d1, d2, D3), 0 - sp);                       // Star-III
                 }
             // Star-III, pairs entering: n_r[d1] x #(d3' entries after r)
             const int64_t after_in = cin_end - (cin_r + D3);
             const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
 #pragma unroll
             for (int d1 = 0; d1 < 2; d1++) {
-                acc[24 + IX(d1, D3, 0)] += n[d1] * (uint64_t)after_o;
-                acc[24 + IX(d1, D3, 1)] += n[d1] * (uint64_t)after_in;
+                add_cell(sacc, 24 + IX(d1, D3, 0), n[d1] * (uint64_t)after_o);
+                add_cell(sacc, 24 + IX(d1, D3, 1), n[d1] * (uint64_t)after_in);
             }
         }
     }
@@ -230,8 +247,8 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
             const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
 #pragma unroll
             for (int d2 = 0; d2 < 2; d2++) {
-                acc[24 + IX(D3, d2, 0)] -= f[d2] * (uint64_t)after_o;
-                acc[24 + IX(D3, d2, 1)] -= f[d2] * (uint64_t)after_in;
+                add_cell(sacc, 24 + IX(D3, d2, 0), 0 - f[d2] * (uint64_t)after_o);
+                add_cell(sacc, 24 + IX(D3, d2, 1), 0 - f[d2] * (uint64_t)after_in);
             }
         }
     }
@@ -243,27 +260,26 @@ __device__ __forceinline__ void star_pair_range(const TEnt *__restrict__ T,
                                                 const int32_t *__restrict__ off, int64_t m,
                                                 int64_t delta, int64_t begin, int64_t end,
                                                 int64_t tid, int64_t nthreads,
-                                                unsigned long long (&acc)[32]) {
+                                                unsigned long long *sacc) {
     const int64_t m2 = 2 * m;
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
         const TEnt e = T[r];
-        if (dir_of(e.nbr)) star_pair_entry<1>(T, off, m2, m, delta, r, e, acc);
-        else star_pair_entry<0>(T, off, m2, m, delta, r, e, acc);
+        if (dir_of(e.nbr)) star_pair_entry<1>(T, off, m2, m, delta, r, e, sacc);
+        else star_pair_entry<0>(T, off, m2, m, delta, r, e, sacc);
     }
 }
 
 __global__ void __launch_bounds__(THREADS)
     k_star_pair(const TEnt *__restrict__ T, const int32_t *__restrict__ off, int64_t m, int64_t delta,
                 int32_t begin, int32_t end, unsigned long long *__restrict__ cells) {
-    unsigned long long acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; c++) acc[c] = 0;
+    __shared__ unsigned long long sacc[32];
+    if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
+    __syncthreads();
     star_pair_range(T, off, m, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                    (int64_t)gridDim.x * blockDim.x, acc);
-    // acc order: Pair, Star-I, Star-II, Star-III -> cells Star[T] at 0.., Pair at 24..
-    block_flush<24, 8>(acc, 0, cells);
-    block_flush<8, 0>(acc, 24, cells);
+                    (int64_t)gridDim.x * blockDim.x, sacc);
+    __syncthreads();
+    flush_star_pair(sacc, cells);
 }
 
 // Raw hash slot of a node pair: (begin, end) of its run, the single edge
@@ -545,6 +561,7 @@ __global__ void __launch_bounds__(THREADS)
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
     __shared__ int32_t cur;
+    __shared__ unsigned long long sacc[32];
     const int32_t nitems = *nitems_ptr;
     const int warp = threadIdx.x >> 5;
     while (true) {
@@ -558,12 +575,11 @@ __global__ void __launch_bounds__(THREADS)
         const int64_t delta = jobs[it.job].delta;
         unsigned long long *cells = jobs[it.job].cells;
         if (it.kind == 0) {
-            unsigned long long acc[32];
-#pragma unroll
-            for (int c = 0; c < 32; c++) acc[c] = 0;
-            star_pair_range(g.T, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x, acc);
-            block_flush<24, 8>(acc, 0, cells);
-            block_flush<8, 0>(acc, 24, cells);
+            if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
+            __syncthreads();
+            star_pair_range(g.T, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
+            __syncthreads();
+            flush_star_pair(sacc, cells);
         } else {
             unsigned long long acc[8];
 #pragma unroll

@@ -143,24 +143,32 @@ __device__ __forceinline__ int digit_of(K k, int shift) {
     return (int)((unsigned)(k >> shift) & (RADIX - 1));
 }
 
-// Per-tile digit histogram (warp-private counters, summed at the end).
+// Per-tile digit histogram: 128-bit loads, warp-private shared counters
+// (plain shared atomics; a skewed digit only contends inside one warp).
 template <typename K, int RS_ITEMS>
 __global__ void __launch_bounds__(RS_THREADS)
     k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ hist,
                  int64_t ntiles) {
     constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+    constexpr int PER_VEC = 16 / sizeof(K);
     __shared__ int h[RS_WARPS][RADIX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&h[0][0])[i] = 0;
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * 32 * RS_ITEMS;
-#pragma unroll 4
-    for (int r = 0; r < RS_ITEMS; r++) {
-        const int64_t i = wbase + r * 32 + lane;
-        const int d = i < n ? digit_of(keys[i], shift) : RADIX;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < RADIX && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
-        __syncwarp();
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int tile_n = (int)(n - tbase < RS_TILE ? n - tbase : RS_TILE);
+    if (tile_n == RS_TILE) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(keys + tbase);
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS / PER_VEC; r++) {
+            const uint4 q = v[r * RS_THREADS + threadIdx.x];
+            const K *kk = reinterpret_cast<const K *>(&q);
+#pragma unroll
+            for (int c = 0; c < PER_VEC; c++) atomicAdd(&h[warp][digit_of(kk[c], shift)], 1);
+        }
+    } else {
+        for (int li = threadIdx.x; li < tile_n; li += RS_THREADS)
+            atomicAdd(&h[warp][digit_of(keys[tbase + li], shift)], 1);
     }
     __syncthreads();
     int c = 0;
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(RS_THREADS)
         const int li = wofs + r * 32 + lane;
         const bool valid = li < tile_n;
         key[r] = valid ? keys_in[tbase + li] : K(0);
-        val[r] = valid ? vals_in[tbase + li] : V(0);
+        val[r] = valid ? vals_in[tbase + li] : V{};
         const int d = valid ? digit_of(key[r], shift) : RADIX;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int before = d < RADIX ? cnt[warp * RADIX + d] : 0;
@@ -252,6 +260,8 @@ void radix_sort_impl(K *keys, V *vals, K *keys_tmp, V *vals_tmp, int64_t n, int 
                      cudaStream_t s, K **keys_out, V **vals_out) {
     K *kin = keys, *kout = keys_tmp;
     V *vin = vals, *vout = vals_tmp;
+    if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(keys_tmp)) & 15)
+        fail(TM_EINVAL, "radix sort: key buffers must be 16-byte aligned");
     if (n > 1 && bits > 0) {
         constexpr int RS_TILE = RsCfg<K, V>::TILE;
         const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
@@ -296,6 +306,13 @@ void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t
                     uint32_t **vals_out) {
     radix_sort_impl<uint64_t, uint32_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
                                         vals_out);
+}
+
+void radix_sort_u32_ent(uint32_t *keys, EntryPayload *vals, uint32_t *keys_tmp,
+                        EntryPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
+                        uint32_t **keys_out, EntryPayload **vals_out) {
+    radix_sort_impl<uint32_t, EntryPayload>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                            vals_out);
 }
 
 void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,

@@ -133,6 +133,16 @@ void radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
                     int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
                     uint32_t **vals_out);
+// Payload of an incident entry while it is sorted by centre: everything its
+// S_u entry needs, so the entry is written without gathers afterwards.
+struct EntryPayload {
+    int64_t t;      // t - t_min
+    uint32_t nbr;   // the other endpoint
+    uint32_t code;  // (rank << 1) | side, side 1 = at the destination (inward)
+};
+void radix_sort_u32_ent(uint32_t *keys, EntryPayload *vals, uint32_t *keys_tmp,
+                        EntryPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
+                        uint32_t **keys_out, EntryPayload **vals_out);
 void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
                         int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
                         uint64_t **vals_out);
