@@ -159,33 +159,37 @@ __global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload
 // node pair's edges as one run in rank order.
 __global__ void k_pair_compact(const TEnt *__restrict__ T, const int32_t *__restrict__ minflag,
                                const int32_t *__restrict__ idx, int64_t n2,
-                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                               uint32_t *__restrict__ keys, PairPayload *__restrict__ vals) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (minflag[p]) {
+            const TEnt e = T[p];
             const int32_t k = idx[p];
-            keys[k] = T[p].nbr & 0x7fffffffu;
-            vals[k] = (uint32_t)p;
+            keys[k] = e.nbr & 0x7fffffffu;
+            PairPayload q;
+            q.pos = (uint32_t)p;
+            q.centre = (uint32_t)e.centre;
+            q.rank = e.rank;
+            q.srcmin = (e.nbr >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
+            vals[k] = q;
         }
     }
 }
 
 // Pair list k: the edge's rank, whether its source is the smaller id, and
 // whether k starts a new node pair.
-__global__ void k_pair_flags(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ ppos,
-                             const TEnt *__restrict__ T, int64_t m, int2 *__restrict__ pl,
-                             int32_t *__restrict__ srcmin, int32_t *__restrict__ head) {
+__global__ void k_pair_flags(const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
+                             int64_t m, int2 *__restrict__ pl, int32_t *__restrict__ srcmin,
+                             int32_t *__restrict__ head) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const TEnt e = T[ppos[k]];
-        pl[k].x = e.rank;
-        srcmin[k] = (e.nbr >> 31) ? 0 : 1;  // o at the smaller endpoint: it is the source
-        head[k] = (k == 0 || pkey[k] != pkey[k - 1] || e.centre != T[ppos[k - 1]].centre) ? 1 : 0;
+        const PairPayload q = pp[k];
+        pl[k].x = q.rank;
+        srcmin[k] = (int32_t)q.srcmin;
+        head[k] = (k == 0 || pkey[k] != pkey[k - 1] || q.centre != pp[k - 1].centre) ? 1 : 0;
     }
 }
 
-// Consecutive edges of one node pair are consecutive same-neighbour entries
-// at both of its nodes: link their entries.
 __global__ void k_pair_cum(const int32_t *__restrict__ cum, int64_t m, int2 *__restrict__ pl) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= m;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -194,17 +198,18 @@ __global__ void k_pair_cum(const int32_t *__restrict__ cum, int64_t m, int2 *__r
     }
 }
 
-__global__ void k_links(const uint32_t *__restrict__ ppos, const int32_t *__restrict__ head,
-                        const int2 *__restrict__ pl, const int32_t *__restrict__ srcmin,
+// Consecutive edges of one node pair are consecutive same-neighbour entries
+// at both of its nodes: link their entries.
+__global__ void k_links(const PairPayload *__restrict__ pp, const int32_t *__restrict__ head,
                         const int32_t *__restrict__ pos_src, const int32_t *__restrict__ pos_dst,
                         int64_t m, TEnt *__restrict__ T) {
     for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (head[k]) continue;
-        const int32_t cur0 = (int32_t)ppos[k], prv0 = (int32_t)ppos[k - 1];
-        const int32_t r = pl[k].x, rp = pl[k - 1].x;
-        const int32_t cur1 = srcmin[k] ? pos_dst[r] : pos_src[r];      // larger endpoint
-        const int32_t prv1 = srcmin[k - 1] ? pos_dst[rp] : pos_src[rp];
+        const PairPayload q = pp[k], qp = pp[k - 1];
+        const int32_t cur0 = (int32_t)q.pos, prv0 = (int32_t)qp.pos;
+        const int32_t cur1 = q.srcmin ? pos_dst[q.rank] : pos_src[q.rank];  // larger endpoint
+        const int32_t prv1 = qp.srcmin ? pos_dst[qp.rank] : pos_src[qp.rank];
         T[cur0].prev = prv0;
         T[prv0].next = cur0;
         T[cur1].prev = prv1;
@@ -221,19 +226,21 @@ __global__ void k_run_begins(const int32_t *__restrict__ head, const int32_t *__
 }
 
 __global__ void k_hash_fill(const int32_t *__restrict__ run_begin, int64_t nruns, int64_t m,
-                            const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ ppos,
-                            const TEnt *__restrict__ T, const int2 *__restrict__ pl,
-                            const int32_t *__restrict__ srcmin, PairSlot *__restrict__ H,
-                            uint32_t mask) {
+                            const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
+                            PairSlot *__restrict__ H, uint32_t mask,
+                            unsigned long long *__restrict__ bloom, uint32_t bloom_mask) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nruns;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t b = run_begin[j];
         int32_t e = j + 1 < nruns ? run_begin[j + 1] : (int32_t)m;
-        const uint64_t key = pair_key((uint32_t)T[ppos[b]].centre, pkey[b]);
+        const PairPayload q = pp[b];
+        const uint64_t key = pair_key(q.centre, pkey[b]);
+        uint32_t word;
+        const uint64_t bits = bloom_bits(key, bloom_mask, &word);
+        atomicOr(&bloom[word], (unsigned long long)bits);
         if (e - b == 1) {  // single edge: kept in the slot
-            const int32_t f = srcmin[b];
-            b = -(pl[b].x + 1);
-            e = f;
+            b = -(q.rank + 1);
+            e = (int32_t)q.srcmin;
         }
         uint32_t h = hash_pair(key) & mask;
         for (uint32_t probe = 0; probe <= mask; probe++) {
@@ -279,23 +286,23 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     int32_t *idx = dev_alloc_n<int32_t>(n2 + 1, s);
     exclusive_scan_i32(minflag, idx, n2, s);
     uint32_t *k1 = dev_alloc_n<uint32_t>(m, s), *k2 = dev_alloc_n<uint32_t>(m, s);
-    uint32_t *v1 = dev_alloc_n<uint32_t>(m, s), *v2 = dev_alloc_n<uint32_t>(m, s);
+    PairPayload *v1 = dev_alloc_n<PairPayload>(m, s), *v2 = dev_alloc_n<PairPayload>(m, s);
     TM_LAUNCH(k_pair_compact, grid_for(n2), 256, 0, s, g.T, minflag, idx, n2, k1, v1);
     dev_free(idx, s);
-    uint32_t *sk, *sv;
-    radix_sort_u32(k1, v1, k2, v2, m, nb, s, &sk, &sv);
+    uint32_t *sk;
+    PairPayload *sv;
+    radix_sort_u32_pair(k1, v1, k2, v2, m, nb, s, &sk, &sv);
 
     int32_t *srcmin = dev_alloc_n<int32_t>(m, s);
     int32_t *head = dev_alloc_n<int32_t>(m, s);
     int32_t *run_id = dev_alloc_n<int32_t>(m + 1, s);
     int32_t *cum = dev_alloc_n<int32_t>(m + 1, s);
-    TM_LAUNCH(k_pair_flags, grid_for(m), 256, 0, s, sk, sv, g.T, m, g.pl, srcmin, head);
+    TM_LAUNCH(k_pair_flags, grid_for(m), 256, 0, s, sk, sv, m, g.pl, srcmin, head);
     exclusive_scan_i32(srcmin, cum, m, s);
     TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, s, cum, m, g.pl);
     dev_free(cum, s);
     exclusive_scan_i32(head, run_id, m, s);
-    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pl, srcmin, g.pos_src, g.pos_dst, m,
-              g.T);
+    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pos_src, g.pos_dst, m, g.T);
     int32_t nruns = 0;
     TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     TM_CUDA(cudaStreamSynchronize(s));
@@ -304,10 +311,16 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     g.hash = dev_alloc_n<PairSlot>((int64_t)cap, s);
     g.hash_mask = (uint32_t)(cap - 1);
     TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * cap, s));
+    // about 8 filter bits per pair, at most 2^22 words (32 MB)
+    uint64_t words = 128;
+    while (words < (uint64_t)nruns / 8 && words < (1ull << 22)) words <<= 1;
+    g.bloom = dev_alloc_n<uint64_t>((int64_t)words, s);
+    g.bloom_mask = (uint32_t)(words - 1);
+    TM_CUDA(cudaMemsetAsync(g.bloom, 0, sizeof(uint64_t) * words, s));
     int32_t *run_begin = dev_alloc_n<int32_t>(nruns + 1, s);
     TM_LAUNCH(k_run_begins, grid_for(m), 256, 0, s, head, run_id, m, run_begin);
-    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, sk, sv, g.T,
-              g.pl, srcmin, g.hash, g.hash_mask);
+    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, sk, sv,
+              g.hash, g.hash_mask, (unsigned long long *)g.bloom, g.bloom_mask);
     dev_free(run_begin, s);
     dev_free(run_id, s);
     dev_free(head, s);
@@ -347,6 +360,7 @@ void free_graph(DevGraph &g, cudaStream_t s) {
     dev_free(g.pos_dst, s);
     dev_free(g.pl, s);
     dev_free(g.hash, s);
+    dev_free(g.bloom, s);
     g = DevGraph();
 }
 
@@ -425,6 +439,9 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         g.hash = dev_alloc_n<PairSlot>(16, s);
         g.hash_mask = 15;
         TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * 16, s));
+        g.bloom = dev_alloc_n<uint64_t>(128, s);
+        g.bloom_mask = 127;
+        TM_CUDA(cudaMemsetAsync(g.bloom, 0, sizeof(uint64_t) * 128, s));
         TM_CUDA(cudaStreamSynchronize(s));
         return;
     }

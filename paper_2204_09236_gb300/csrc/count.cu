@@ -314,8 +314,19 @@ struct PairCounts {
     int32_t nb, na, fb, fa;
 };
 
+// L2 eviction policy "keep": the Bloom filter is read by every probe.
+__device__ __forceinline__ uint64_t load_keep(const uint64_t *p) {
+    uint64_t v, pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int32_t rank_lo,
                                             int32_t rank_hi, int32_t at, PairCounts &c) {
+    uint32_t word;
+    const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
+    if ((load_keep(g.bloom + word) & bits) != bits) return false;  // the pair never met
     const int2 run = find_pair(g.hash, g.hash_mask, key);
     if (run.x < 0) {  // single edge kept in the slot
         const int32_t r1 = -run.x - 1;

@@ -102,7 +102,22 @@ struct DevGraph {
     int2 *pl = nullptr;
     PairSlot *hash = nullptr;   // open addressing, linear probing
     uint32_t hash_mask = 0;
+    // blocked Bloom filter of the node pairs (three bits in one 64-bit word
+    // per pair): most join probes ask about pairs that never met, and this
+    // filter (at most 32 MB, kept in L2) answers them without touching the hash
+    uint64_t *bloom = nullptr;
+    uint32_t bloom_mask = 0;
 };
+
+// Word index and bit mask of a pair key in the Bloom filter.
+__host__ __device__ inline uint64_t bloom_bits(uint64_t key, uint32_t mask, uint32_t *word) {
+    uint64_t h = key * 0x9e3779b97f4a7c15ull;
+    h ^= h >> 29;
+    h *= 0xbf58476d1ce4e5b9ull;
+    h ^= h >> 32;
+    *word = (uint32_t)h & mask;
+    return (1ull << ((h >> 40) & 63)) | (1ull << ((h >> 46) & 63)) | (1ull << ((h >> 52) & 63));
+}
 
 __host__ __device__ inline uint64_t pair_key(uint32_t a, uint32_t b) {
     return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
@@ -140,6 +155,18 @@ struct EntryPayload {
     uint32_t nbr;   // the other endpoint
     uint32_t code;  // (rank << 1) | side, side 1 = at the destination (inward)
 };
+// Payload of an edge while the pair list is sorted: the T position of its
+// entry at the smaller endpoint, that endpoint, the edge's rank and whether
+// the smaller endpoint is its source.
+struct PairPayload {
+    uint32_t pos;
+    uint32_t centre;
+    int32_t rank;
+    uint32_t srcmin;
+};
+void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
+                         PairPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
+                         uint32_t **keys_out, PairPayload **vals_out);
 void radix_sort_u32_ent(uint32_t *keys, EntryPayload *vals, uint32_t *keys_tmp,
                         EntryPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
                         uint32_t **keys_out, EntryPayload **vals_out);
