@@ -131,6 +131,7 @@ __global__ void k_dir_flags(const EntryPayload *__restrict__ pl, int64_t n2,
 
 __global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload *__restrict__ pl,
                          const int32_t *__restrict__ cin, int64_t n2, TEnt *__restrict__ T,
+                         int64_t *__restrict__ tt, uint2 *__restrict__ tn,
                          int32_t *__restrict__ pos_src, int32_t *__restrict__ pos_dst,
                          int32_t *__restrict__ minflag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
@@ -148,6 +149,8 @@ __global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload
         e.next = -1;
         e.centre = (int32_t)c;
         T[p] = e;
+        tt[p] = e.t;
+        tn[p] = make_uint2(e.nbr, (uint32_t)rank);
         if (side) pos_dst[rank] = (int32_t)p;
         else pos_src[rank] = (int32_t)p;
         minflag[p] = c < q.nbr ? 1 : 0;
@@ -355,6 +358,8 @@ void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevG
 
 void free_graph(DevGraph &g, cudaStream_t s) {
     dev_free(g.T, s);
+    dev_free(g.tt, s);
+    dev_free(g.tn, s);
     dev_free(g.off, s);
     dev_free(g.pos_src, s);
     dev_free(g.pos_dst, s);
@@ -430,6 +435,8 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
 
     g.off = dev_alloc_n<int32_t>(n + 1, s);
     g.T = dev_alloc_n<TEnt>(2 * m, s);
+    g.tt = dev_alloc_n<int64_t>(2 * m, s);
+    g.tn = dev_alloc_n<uint2>(2 * m, s);
     g.pos_src = dev_alloc_n<int32_t>(m, s);
     g.pos_dst = dev_alloc_n<int32_t>(m, s);
     g.pl = dev_alloc_n<int2>(m + 1, s);
@@ -476,8 +483,8 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
         TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
         exclusive_scan_i32(flags, cin, n2, s);
-        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.pos_src, g.pos_dst,
-                  minflag);
+        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.tt, g.tn, g.pos_src,
+                  g.pos_dst, minflag);
         dev_free(flags, s);
         dev_free(cin, s);
         dev_free(k1, s);

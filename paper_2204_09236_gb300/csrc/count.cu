@@ -60,14 +60,14 @@ __device__ __forceinline__ int32_t warp_incl_scan_i32(int32_t v) {
 }
 __device__ __forceinline__ uint32_t node_of(uint32_t nbr) { return nbr & 0x7fffffffu; }
 
-// First position p in [b, r] with T[p].t >= bound; T[r].t >= bound holds.
-__device__ __forceinline__ int32_t gallop_lo(const TEnt *__restrict__ T, int32_t b, int32_t r,
+// First position p in [b, r] with tt[p] >= bound; tt[r] >= bound holds.
+__device__ __forceinline__ int32_t gallop_lo(const int64_t *__restrict__ tt, int32_t b, int32_t r,
                                              int64_t bound) {
     int32_t hi = r, lo = b - 1, step = 1;
     while (true) {
         int32_t p = hi - step;
         if (p < b) break;
-        if (T[p].t < bound) {
+        if (tt[p] < bound) {
             lo = p;
             break;
         }
@@ -76,20 +76,20 @@ __device__ __forceinline__ int32_t gallop_lo(const TEnt *__restrict__ T, int32_t
     }
     while (hi - lo > 1) {
         int32_t mid = lo + ((hi - lo) >> 1);
-        if (T[mid].t >= bound) hi = mid;
+        if (tt[mid] >= bound) hi = mid;
         else lo = mid;
     }
     return hi;
 }
 
-// Last position q in [r, e) with T[q].t - tr <= delta.
-__device__ __forceinline__ int32_t gallop_hi(const TEnt *__restrict__ T, int32_t r, int32_t e,
+// Last position q in [r, e) with tt[q] - tr <= delta.
+__device__ __forceinline__ int32_t gallop_hi(const int64_t *__restrict__ tt, int32_t r, int32_t e,
                                              int64_t tr, int64_t delta) {
     int32_t lo = r, hi = e, step = 1;
     while (true) {
         int32_t q = lo + step;
         if (q >= e) break;
-        if (T[q].t - tr > delta) {
+        if (tt[q] - tr > delta) {
             hi = q;
             break;
         }
@@ -98,7 +98,7 @@ __device__ __forceinline__ int32_t gallop_hi(const TEnt *__restrict__ T, int32_t
     }
     while (hi - lo > 1) {
         int32_t mid = lo + ((hi - lo) >> 1);
-        if (T[mid].t - tr <= delta) lo = mid;
+        if (tt[mid] - tr <= delta) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -152,6 +152,7 @@ __device__ __forceinline__ void flush_star_pair(const unsigned long long *sacc,
 
 template <int D3>
 __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
+                                                const int64_t *__restrict__ tt,
                                                 const int32_t *__restrict__ off, int64_t m2,
                                                 int64_t m, int64_t delta, int32_t r,
                                                 const TEnt &e, unsigned long long *sacc) {
@@ -160,12 +161,12 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
     const int32_t seg_b = off[u], seg_end = off[u + 1];
     // W(r) and F(r) bounds from the neighbouring entries of S_u (local reads);
     // the same-neighbour links are followed only when they land inside.
-    const bool wnd_back = e.prev >= 0 && r > seg_b && tr - T[r - 1].t <= delta;
-    const bool wnd_fwd = e.next >= 0 && r + 1 < seg_end && T[r + 1].t - tr <= delta;
+    const bool wnd_back = e.prev >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
+    const bool wnd_fwd = e.next >= 0 && r + 1 < seg_end && tt[r + 1] - tr <= delta;
     if (!wnd_back && !wnd_fwd) return;
     const int64_t cin_end = seg_end < m2 ? (int64_t)T[seg_end].cin : m;
     if (wnd_back) {
-        const int32_t lo = gallop_lo(T, seg_b, r, tr - delta);
+        const int32_t lo = gallop_lo(tt, seg_b, r, tr - delta);
         if (e.prev >= lo) {
             // per direction d of the run entries: n_d (count), c2s_{d,d'} (pairs),
             // X_{d,d'} (d' entries strictly between a and r), Y_{d,d'} (d' entries
@@ -228,7 +229,7 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
         }
     }
     if (wnd_fwd) {
-        const int32_t hi = gallop_hi(T, r, seg_end, tr, delta);
+        const int32_t hi = gallop_hi(tt, r, seg_end, tr, delta);
         if (e.next <= hi) {
             // same-neighbour entries inside F(r): pairs leaving after hi(r)
             uint64_t f0 = 0, f1 = 0;
@@ -257,6 +258,7 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
 // Star/Pair contributions of the entries [begin, end) of g.T, visited by
 // threads tid, tid + nthreads, ...
 __device__ __forceinline__ void star_pair_range(const TEnt *__restrict__ T,
+                                                const int64_t *__restrict__ tt,
                                                 const int32_t *__restrict__ off, int64_t m,
                                                 int64_t delta, int64_t begin, int64_t end,
                                                 int64_t tid, int64_t nthreads,
@@ -265,18 +267,19 @@ __device__ __forceinline__ void star_pair_range(const TEnt *__restrict__ T,
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
         const TEnt e = T[r];
-        if (dir_of(e.nbr)) star_pair_entry<1>(T, off, m2, m, delta, r, e, sacc);
-        else star_pair_entry<0>(T, off, m2, m, delta, r, e, sacc);
+        if (dir_of(e.nbr)) star_pair_entry<1>(T, tt, off, m2, m, delta, r, e, sacc);
+        else star_pair_entry<0>(T, tt, off, m2, m, delta, r, e, sacc);
     }
 }
 
 __global__ void __launch_bounds__(THREADS)
-    k_star_pair(const TEnt *__restrict__ T, const int32_t *__restrict__ off, int64_t m, int64_t delta,
-                int32_t begin, int32_t end, unsigned long long *__restrict__ cells) {
+    k_star_pair(const TEnt *__restrict__ T, const int64_t *__restrict__ tt,
+                const int32_t *__restrict__ off, int64_t m, int64_t delta, int32_t begin,
+                int32_t end, unsigned long long *__restrict__ cells) {
     __shared__ unsigned long long sacc[32];
     if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
     __syncthreads();
-    star_pair_range(T, off, m, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+    star_pair_range(T, tt, off, m, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                     (int64_t)gridDim.x * blockDim.x, sacc);
     __syncthreads();
     flush_star_pair(sacc, cells);
@@ -367,18 +370,18 @@ struct TriEdge {
 // (dj = 0); at the destination w it is inward (dj = 1). A match ranked after
 // the item is centred at the item's centre, one ranked before it at the big
 // window's centre.
-__device__ __forceinline__ void tri_probe(const DevGraph &g, const TriEdge &E, const TEnt &it,
+__device__ __forceinline__ void tri_probe(const DevGraph &g, const TriEdge &E, const uint2 it,
                                           unsigned long long (&acc)[8]) {
-    const uint32_t x = node_of(it.nbr);
+    const uint32_t x = node_of(it.x);
     const uint32_t big = E.small_is_u ? E.w : E.u;
     if (x == big) return;  // an edge of the pair (u, w) itself
     PairCounts c;
-    if (!pair_counts(g, pair_key(big, x), E.rank_lo_big, E.rank_j, it.rank, c)) return;
+    if (!pair_counts(g, pair_key(big, x), E.rank_lo_big, E.rank_j, (int32_t)it.y, c)) return;
     // a big-side edge big -> x is outward at big and inward at x
     const bool big_is_min = big < x;
     const int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
     const int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
-    const int di = dir_of(it.nbr);                              // item w.r.t. its centre
+    const int di = dir_of(it.x);                                // item w.r.t. its centre
     if (E.small_is_u) {
         // item a in W_u (node x), matches k in W_w.
         // after a: centre u, (e_i = a, e_k = k): Tri[II][d_a][0][dir of k w.r.t. x]
@@ -439,13 +442,13 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
             if (dir_of(e.nbr) == 0) {
                 const uint32_t u = (uint32_t)e.centre;
                 const int32_t sb = g.off[u];
-                if (r > sb && e.t - T[r - 1].t <= delta) {
+                if (r > sb && e.t - g.tt[r - 1] <= delta) {
                     const uint32_t w = node_of(e.nbr);
                     const int32_t twin = g.pos_dst[e.rank];
                     const int32_t wb = g.off[w];
-                    if (twin > wb && e.t - T[twin - 1].t <= delta) {
-                        const int32_t lo_u = gallop_lo(T, sb, (int32_t)r, e.t - delta);
-                        const int32_t lo_w = gallop_lo(T, wb, twin, e.t - delta);
+                    if (twin > wb && e.t - g.tt[twin - 1] <= delta) {
+                        const int32_t lo_u = gallop_lo(g.tt, sb, (int32_t)r, e.t - delta);
+                        const int32_t lo_w = gallop_lo(g.tt, wb, twin, e.t - delta);
                         const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
                         E.u = u;
                         E.w = w;
@@ -453,7 +456,7 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
                         E.small_is_u = wu <= ww;
                         E.small_lo = E.small_is_u ? lo_u : lo_w;
                         E.work = E.small_is_u ? wu : ww;
-                        E.rank_lo_big = T[E.small_is_u ? lo_w : lo_u].rank;
+                        E.rank_lo_big = (int32_t)g.tn[E.small_is_u ? lo_w : lo_u].y;
                     }
                 }
             }
@@ -476,7 +479,7 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
                 }
                 const TriEdge &B = edges[lo];
                 const int32_t k = j - (incl[lo] - B.work);
-                tri_probe(g, B, T[B.small_lo + k], acc);
+                tri_probe(g, B, g.tn[B.small_lo + k], acc);
             }
         }
         __syncwarp();
@@ -521,10 +524,10 @@ __global__ void __launch_bounds__(THREADS)
         const TEnt e = T[r];
         const int dj = dir_of(e.nbr);
         const uint32_t u = (uint32_t)e.centre, w = node_of(e.nbr);
-        const int32_t lo_u = gallop_lo(T, g.off[u], r, e.t - delta);
+        const int32_t lo_u = gallop_lo(g.tt, g.off[u], r, e.t - delta);
         if (lo_u == r) continue;
         const int32_t twin = dj ? g.pos_src[e.rank] : g.pos_dst[e.rank];
-        const int32_t lo_w = gallop_lo(T, g.off[w], twin, e.t - delta);
+        const int32_t lo_w = gallop_lo(g.tt, g.off[w], twin, e.t - delta);
         if (lo_w == twin) continue;
         const int32_t rank_lo_w = T[lo_w].rank;
         // items a of W_u, matches k of W_w ranked after a: centred at u
@@ -588,7 +591,8 @@ __global__ void __launch_bounds__(THREADS)
         if (it.kind == 0) {
             if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
             __syncthreads();
-            star_pair_range(g.T, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
+            star_pair_range(g.T, g.tt, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x,
+                            sacc);
             __syncthreads();
             flush_star_pair(sacc, cells);
         } else {
@@ -641,8 +645,8 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     if (blocks > cap) blocks = cap;
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.off, g.m, delta, begin, end,
-                  dev_cells);
+        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, begin,
+                  end, dev_cells);
     }
     {
         PhaseTimer pt(TM_PH_TRI, s);
@@ -663,7 +667,7 @@ void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.off, g.m, delta, 0,
+    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, 0,
               (int32_t)n, dev_cells);
     TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);

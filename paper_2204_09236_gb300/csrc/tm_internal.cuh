@@ -93,6 +93,10 @@ struct DevGraph {
     int32_t n = 0;
     int64_t tmin = 0;
     TEnt *T = nullptr;          // 2m entries, grouped by centre, (t, id) order inside
+    // dense copies of two fields of T, for the window searches (tt: t) and
+    // the join items (tn: {nbr | dir << 31, rank}) of the counting kernels
+    int64_t *tt = nullptr;
+    uint2 *tn = nullptr;
     int32_t *off = nullptr;     // n+1: S_u = T[off[u], off[u+1])
     int32_t *pos_src = nullptr; // m, by rank: T position of the edge at its source
     int32_t *pos_dst = nullptr; // m, by rank: T position at its destination
