@@ -115,6 +115,25 @@ int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, i
                      uint64_t cells[56]);
 
 /*
+ * Category-selective counting (the per-category variants FAST-Pair /
+ * FAST-Tri that the paper times separately, Sec. V-C, Table 3): what =
+ * TM_SELECT_STAR_PAIR runs only Algorithm 1's counters (Star and Pair
+ * cells), TM_SELECT_TRI only Algorithm 2's (Tri cells), both = all 56.
+ * cells: host uint64[56]; the cells of the category not selected are 0.
+ */
+#define TM_SELECT_STAR_PAIR 1
+#define TM_SELECT_TRI 2
+int tm_count_select(const tm_graph *g, int64_t delta, int32_t what, uint64_t cells[56]);
+
+/*
+ * Counts one graph for k windows deltas[0..k) in one batched launch (all k
+ * counts share the persistent queue); out[i*36 .. i*36+36) as in tm_count.
+ * The paper's delta sensitivity experiment (Sec. V-E, Fig. 11(a)) is this
+ * call over a list of deltas.
+ */
+int tm_count_multi(const tm_graph *g, const int64_t *deltas, int32_t k, uint64_t *out);
+
+/*
  * Folds 56 raw cells into the 36 classes (out[36] as above) on the host.
  * Returns the number of classes whose isomorphic cells disagree (the pair
  * mirror cells, Sec. IV-A; the three triangle cells of a class, one per

@@ -312,6 +312,21 @@ int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, i
     });
 }
 
+int tm_count_select(const tm_graph *g, int64_t delta, int32_t what, uint64_t cells[56]) {
+    return guarded([&] {
+        check_count_args(g, delta);
+        if (!cells || what < 1 || what > 3) fail(TM_EINVAL, "bad selection");
+        cudaStream_t s = lib_stream();
+        unsigned long long *d = dev_alloc_n<unsigned long long>(NCELLS, s);
+        TM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NCELLS, s));
+        launch_count_parts(g->g, delta, (what & TM_SELECT_STAR_PAIR) != 0,
+                           (what & TM_SELECT_TRI) != 0, d, s);
+        TM_CUDA(cudaMemcpyAsync(cells, d, sizeof(uint64_t) * NCELLS, cudaMemcpyDeviceToHost, s));
+        dev_free(d, s);
+        TM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
 int tm_merge(const uint64_t cells[56], uint64_t out[36]) {
     if (!cells || !out) {
         set_error(TM_EINVAL, "NULL argument");

@@ -414,6 +414,25 @@ tm_graph *tm_build_many(int32_t k, const int32_t *const *src, const int32_t *con
     return rc == TM_OK ? h : nullptr;
 }
 
+int tm_count_multi(const tm_graph *g, const int64_t *deltas, int32_t k, uint64_t *out) {
+    return guard([&] {
+        check_graph(g);
+        if (k < 0 || (k > 0 && (!deltas || !out))) fail(TM_EINVAL, "bad multi-delta arguments");
+        if (k == 0) return;
+        std::vector<JobSpec> jobs;
+        for (int32_t i = 0; i < k; i++) {
+            if (deltas[i] < 0) fail(TM_EINVAL, "delta must be >= 0");
+            jobs.push_back(JobSpec{&g->g, deltas[i], 0, (int32_t)(2 * g->g.m)});
+        }
+        int64_t ie;
+        int32_t bps;
+        current_config(ie, bps);
+        std::vector<uint64_t> cells;
+        run_jobs(jobs, cells, ie, bps);
+        for (int32_t i = 0; i < k; i++) tm_merge(cells.data() + (size_t)NCELLS * i, out + 36 * (size_t)i);
+    });
+}
+
 int32_t tm_graph_components(const tm_graph *g) {
     if (!g) return -1;
     return g->comp_toff.empty() ? 1 : (int32_t)g->comp_toff.size() - 1;

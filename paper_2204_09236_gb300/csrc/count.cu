@@ -660,6 +660,25 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     }
 }
 
+void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,
+                        unsigned long long *dev_cells, cudaStream_t s) {
+    const int64_t n = 2 * g.m;
+    if (n == 0) return;
+    int64_t blocks = (n + THREADS - 1) / THREADS;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (star_pair) {
+        PhaseTimer pt(TM_PH_STAR_PAIR, s);
+        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, 0,
+                  (int32_t)n, dev_cells);
+    }
+    if (tri) {
+        PhaseTimer pt(TM_PH_TRI, s);
+        TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
+        TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
+    }
+}
+
 void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,
                           cudaStream_t s) {
     const int64_t n = 2 * g.m;

@@ -43,6 +43,8 @@ _lib.tm_graph_edges.argtypes = [_P]
 _lib.tm_launch_count.restype = ctypes.c_uint64
 _lib.tm_count_noalloc.argtypes = [_P, _P, ctypes.c_int32, _P, _P]
 _lib.tm_count_batch.argtypes = [_P, _P, ctypes.c_int32, _P]
+_lib.tm_count_select.argtypes = [_P, _i64, ctypes.c_int32, _P]
+_lib.tm_count_multi.argtypes = [_P, _P, ctypes.c_int32, _P]
 _lib.tm_build_many.restype = _P
 _lib.tm_build_many.argtypes = [ctypes.c_int32, _P, _P, _P, _P]
 _lib.tm_graph_components.restype = ctypes.c_int32
@@ -255,6 +257,25 @@ def tm_count_batch(graphs, deltas):
     return out[:n].reshape(n, 6, 6)
 
 
+SELECT_STAR_PAIR, SELECT_TRI = 1, 2
+
+
+def tm_count_select(g, delta, what):
+    """Only the Star/Pair counters (what=1), only the Tri counters (what=2),
+    or both (3); returns (star, pair, tri)."""
+    cells = np.zeros(56, np.uint64)
+    _check(_lib.tm_count_select(g.handle, int(delta), int(what), cells.ctypes.data_as(_P)))
+    return split_cells(cells)
+
+
+def tm_count_multi(g, deltas):
+    """One graph, several windows, one batched launch; (k, 6, 6) uint64."""
+    d = np.ascontiguousarray(deltas, np.int64)
+    out = np.zeros((max(len(d), 1), 36), np.uint64)
+    _check(_lib.tm_count_multi(g.handle, d.ctypes.data_as(_P), len(d), out.ctypes.data_as(_P)))
+    return out[:len(d)].reshape(len(d), 6, 6)
+
+
 def tm_build_many(graphs):
     """One device graph whose components are the given (src, dst, t) graphs."""
     k = len(graphs)
@@ -431,6 +452,8 @@ count_async = tm_count_async
 count_centres = tm_count_centres
 count_noalloc = tm_count_noalloc
 count_batch = tm_count_batch
+count_select = tm_count_select
+count_multi = tm_count_multi
 build_many = tm_build_many
 count_many = tm_count_many
 graph_components = tm_graph_components

@@ -86,3 +86,21 @@ def test_build_many_rejects_bad_component(tm):
     with pytest.raises(tm.TmError) as e:
         tm.build_many([ok, bad])
     assert e.value.code == tm.TM_EINVAL
+
+
+def test_count_select_and_multi(tm):
+    s, d, t = synth.hub(scale=0.001)
+    g = tm.build(s, d, t)
+    S, P, Q = tm.count_raw(g, 3600)
+    s1, p1, q1 = tm.count_select(g, 3600, tm.SELECT_STAR_PAIR)
+    assert (s1 == S).all() and (p1 == P).all() and q1.sum() == 0
+    s2, p2, q2 = tm.count_select(g, 3600, tm.SELECT_TRI)
+    assert s2.sum() == 0 and p2.sum() == 0 and (q2 == Q).all()
+    deltas = [0, 60, 600, 3600, 86400, 10 ** 7]
+    multi = tm.count_multi(g, deltas)
+    for i, dl in enumerate(deltas):
+        assert (multi[i] == tm.count(g, dl)).all(), dl
+        assert (multi[i] == oracle_classes(s, d, t, dl)).all(), dl
+    # monotone in delta, class by class
+    assert (np.diff(multi.astype(np.int64), axis=0) >= 0).all()
+    g.free()
