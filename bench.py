@@ -40,6 +40,11 @@ UNIT = "edges/s"
 ALGO_BYTES = {"star_pair": 32, "tri": 48, "time_sort": 16, "incident": 48, "pairs": 32,
               "validate": 16}
 
+# DRAM bytes (read + write) of one k_tri launch on the full workload, from one
+# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# (profiles/k_tri_dram_large_60M.md); None until captured for the current kernel
+TRI_TRAFFIC = {}
+
 WORKLOADS = {
     "large": dict(desc="large: 2.5M nodes, 60M edges, Zipf(2.0) degree law, out-degree cap 2e5, "
                        "8 years, diurnal rate", delta=86400),
@@ -183,7 +188,7 @@ def run_batch(args, rank, world, dist):
         return (time.perf_counter() - st) / steps, out
 
     tune = None
-    if args.tune:
+    if not args.no_tune:
         g = tm.build_many(views)
         ie, bps, tms = tm.tune_batch(g, deltas, reps=2)
         g.free()
@@ -361,7 +366,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-count-only", action="store_true")
-    ap.add_argument("--tune", action="store_true", help="batch workload: run the autotuner first")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch workload: skip the autotuner (use the library defaults)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--seconds", type=float, default=60.0, help="serve: trace length")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device budget")
@@ -436,14 +442,22 @@ def main():
     ms_step = ms / args.steps
     value = world * m / (ms_step / 1e3)
 
-    # per-phase device times (events on the launching stream)
+    # per-phase device times (events on the launching stream, one pair per
+    # phase and step); the Tri join kernel is the largest single kernel of
+    # the step (profiles/launch_list_large_60M.md)
     ph = {k: v[0] / max(v[1], 1) for k, v in phases.items()}
-    dom = max(ph, key=lambda k: ph[k])
     peak, peak_kind = measured_peak()
-    achieved = ALGO_BYTES[dom] * m / (ph[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                "algo_bytes_per_edge": ALGO_BYTES[dom]}
+
+    def gbs(phase):
+        return ALGO_BYTES[phase] * m / (ph[phase] / 1e3) / 1e9 if ph.get(phase) else None
+
+    achieved = gbs("tri")
+    roofline = {"bound": "hbm", "kernel": "k_tri", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": TRI_TRAFFIC.get(args.workload) if args.scale == 1.0 else None,
+                "algo_bytes_per_edge": ALGO_BYTES["tri"], "kernel_ms": ph["tri"],
+                "phases": {k: {"ms": round(ph[k], 4), "algo_GBps": round(gbs(k), 1),
+                               "frac": round(gbs(k) / peak, 4)} for k in ph if ph[k] > 0}}
 
     # count only (graph resident)
     count_ms = None

@@ -22,9 +22,11 @@ void free_graph(DevGraph &g, cudaStream_t s);
 namespace {
 
 // Process-wide batching parameters (set by tm_batch_config / tm_tune_batch).
+// Defaults: what tm_tune_batch picked on the 512-graph batch workload; small
+// items keep a window-heavy range from becoming the last block standing.
 std::mutex g_cfg_mu;
-int64_t g_item_entries = 32768;
-int32_t g_blocks_per_sm = 0;  // 0: as many as fit
+int64_t g_item_entries = 4096;
+int32_t g_blocks_per_sm = 2;  // 0: as many as fit
 
 struct JobSpec {
     const DevGraph *g;
