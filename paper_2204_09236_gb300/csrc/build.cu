@@ -10,6 +10,7 @@
 //   5. stable radix sort of the edges by node pair: every E_(v,w) (Alg. 2) is
 //      a run of the pair list in rank order; a hash maps a pair to its run
 //   6. links between consecutive same-neighbour entries of a centre
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -132,8 +133,7 @@ __global__ void k_dir_flags(const EntryPayload *__restrict__ pl, int64_t n2,
 __global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload *__restrict__ pl,
                          const int32_t *__restrict__ cin, int64_t n2, TEnt *__restrict__ T,
                          int64_t *__restrict__ tt, uint2 *__restrict__ tn,
-                         int32_t *__restrict__ pos_src, int32_t *__restrict__ pos_dst,
-                         int32_t *__restrict__ minflag) {
+                         uint32_t *__restrict__ codes, int32_t *__restrict__ minflag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         const EntryPayload q = pl[p];
@@ -151,9 +151,26 @@ __global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload
         T[p] = e;
         tt[p] = e.t;
         tn[p] = make_uint2(e.nbr, (uint32_t)rank);
-        if (side) pos_dst[rank] = (int32_t)p;
-        else pos_src[rank] = (int32_t)p;
+        codes[p] = q.code;
         minflag[p] = c < q.nbr ? 1 : 0;
+    }
+}
+
+// pos_src / pos_dst[rank] = T position of the edge's entry at its source /
+// destination, for the ranks in [rlo, rhi) only. The build runs this once per
+// rank range whose part of the two arrays fits in L2, so the random 4-byte
+// stores merge in L2 instead of each costing a DRAM read-modify-write.
+__global__ void k_pos_scatter(const uint32_t *__restrict__ codes, int64_t n2, uint32_t rlo,
+                              uint32_t rhi, int32_t *__restrict__ pos_src,
+                              int32_t *__restrict__ pos_dst) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = __ldcs(codes + p);  // streamed: evict first, keep L2 for the stores
+        const uint32_t r = c >> 1;
+        if (r >= rlo && r < rhi) {
+            if (c & 1u) pos_dst[r] = (int32_t)p;
+            else pos_src[r] = (int32_t)p;
+        }
     }
 }
 
@@ -483,8 +500,14 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
         TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
         exclusive_scan_i32(flags, cin, n2, s);
-        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.tt, g.tn, g.pos_src,
-                  g.pos_dst, minflag);
+        uint32_t *codes = reinterpret_cast<uint32_t *>(flags);  // flags are consumed by the scan
+        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.tt, g.tn, codes,
+                  minflag);
+        // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
+        const int64_t ranks_per_pass = (int64_t)8 << 20;
+        for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
+            TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
+                      (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);
         dev_free(flags, s);
         dev_free(cin, s);
         dev_free(k1, s);
