@@ -245,10 +245,14 @@ __global__ void k_run_begins(const int32_t *__restrict__ head, const int32_t *__
     }
 }
 
-__global__ void k_hash_fill(const int32_t *__restrict__ run_begin, int64_t nruns, int64_t m,
-                            const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
-                            PairSlot *__restrict__ H, uint32_t mask,
-                            unsigned long long *__restrict__ bloom, uint32_t bloom_mask) {
+// One insertion record per node pair (a single-edge pair keeps its edge:
+// begin = -(rank + 1), end = source-is-min), keyed by the slot region it
+// hashes to; also sets the pair's bits in the Bloom filter.
+__global__ void k_hash_records(const int32_t *__restrict__ run_begin, int64_t nruns, int64_t m,
+                               const uint32_t *__restrict__ pkey,
+                               const PairPayload *__restrict__ pp, uint32_t mask, int region_shift,
+                               uint32_t *__restrict__ region, HashRecord *__restrict__ rec,
+                               unsigned long long *__restrict__ bloom, uint32_t bloom_mask) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nruns;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t b = run_begin[j];
@@ -258,18 +262,32 @@ __global__ void k_hash_fill(const int32_t *__restrict__ run_begin, int64_t nruns
         uint32_t word;
         const uint64_t bits = bloom_bits(key, bloom_mask, &word);
         atomicOr(&bloom[word], (unsigned long long)bits);
-        if (e - b == 1) {  // single edge: kept in the slot
+        if (e - b == 1) {
             b = -(q.rank + 1);
             e = (int32_t)q.srcmin;
         }
-        uint32_t h = hash_pair(key) & mask;
+        region[j] = (hash_pair(key) & mask) >> region_shift;
+        rec[j] = HashRecord{key, b, e};
+    }
+}
+
+// Inserts the records of one slot region ([start[r], start[r+1]) of the
+// region-sorted records): the region's part of the table stays in L2 while
+// its random compare-and-swaps run.
+__global__ void k_hash_insert(const HashRecord *__restrict__ rec, const int32_t *__restrict__ start,
+                              int r, PairSlot *__restrict__ H, uint32_t mask) {
+    const int32_t lo = start[r], hi = start[r + 1];
+    for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const HashRecord q = rec[j];
+        uint32_t h = hash_pair(q.key) & mask;
         for (uint32_t probe = 0; probe <= mask; probe++) {
             unsigned long long prev =
                 atomicCAS((unsigned long long *)&H[h].key, (unsigned long long)EMPTY_KEY,
-                          (unsigned long long)key);
+                          (unsigned long long)q.key);
             if (prev == EMPTY_KEY) {
-                H[h].begin = b;
-                H[h].end = e;
+                H[h].begin = q.begin;
+                H[h].end = q.end;
                 break;
             }
             h = (h + 1) & mask;
@@ -339,8 +357,30 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     TM_CUDA(cudaMemsetAsync(g.bloom, 0, sizeof(uint64_t) * words, s));
     int32_t *run_begin = dev_alloc_n<int32_t>(nruns + 1, s);
     TM_LAUNCH(k_run_begins, grid_for(m), 256, 0, s, head, run_id, m, run_begin);
-    TM_LAUNCH(k_hash_fill, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, sk, sv,
-              g.hash, g.hash_mask, (unsigned long long *)g.bloom, g.bloom_mask);
+    // regions of 2^22 slots (64 MB of table): insertion records are grouped
+    // by region with one radix pass, then inserted one region at a time
+    int cap_bits = 0;
+    while ((1ull << cap_bits) < cap) cap_bits++;
+    const int region_shift = cap_bits > 22 ? 22 : cap_bits;
+    const int nregions = 1 << (cap_bits - region_shift);
+    uint32_t *rk1 = dev_alloc_n<uint32_t>(nruns, s), *rk2 = dev_alloc_n<uint32_t>(nruns, s);
+    HashRecord *rv1 = dev_alloc_n<HashRecord>(nruns, s), *rv2 = dev_alloc_n<HashRecord>(nruns, s);
+    int32_t *rstart = dev_alloc_n<int32_t>(nregions + 1, s);
+    TM_LAUNCH(k_hash_records, grid_for(nruns), 256, 0, s, run_begin, (int64_t)nruns, m, sk, sv,
+              g.hash_mask, region_shift, rk1, rv1, (unsigned long long *)g.bloom, g.bloom_mask);
+    uint32_t *rks;
+    HashRecord *rvs;
+    radix_sort_u32_rec(rk1, rv1, rk2, rv2, nruns, bits_for((uint64_t)(nregions - 1)), s, &rks, &rvs);
+    TM_LAUNCH(k_offsets, grid_for((int64_t)nruns + 1), 256, 0, s, rks, (int64_t)nruns,
+              (int64_t)nregions, rstart);
+    for (int r = 0; r < nregions; r++)
+        TM_LAUNCH(k_hash_insert, grid_for((int64_t)nruns / nregions + 1), 256, 0, s, rvs, rstart, r,
+                  g.hash, g.hash_mask);
+    dev_free(rk1, s);
+    dev_free(rk2, s);
+    dev_free(rv1, s);
+    dev_free(rv2, s);
+    dev_free(rstart, s);
     dev_free(run_begin, s);
     dev_free(run_id, s);
     dev_free(head, s);

@@ -308,6 +308,13 @@ void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t
                                         vals_out);
 }
 
+void radix_sort_u32_rec(uint32_t *keys, HashRecord *vals, uint32_t *keys_tmp, HashRecord *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
+                        HashRecord **vals_out) {
+    radix_sort_impl<uint32_t, HashRecord>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
+                                          vals_out);
+}
+
 void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
                          PairPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
                          uint32_t **keys_out, PairPayload **vals_out) {

@@ -168,6 +168,15 @@ struct PairPayload {
     int32_t rank;
     uint32_t srcmin;
 };
+// One pair-hash insertion: the pair key and its run (or single edge).
+struct HashRecord {
+    uint64_t key;
+    int32_t begin;
+    int32_t end;
+};
+void radix_sort_u32_rec(uint32_t *keys, HashRecord *vals, uint32_t *keys_tmp, HashRecord *vals_tmp,
+                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
+                        HashRecord **vals_out);
 void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
                          PairPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
                          uint32_t **keys_out, PairPayload **vals_out);
