@@ -78,37 +78,23 @@ __global__ void k_time_keys(const int32_t *__restrict__ src, const int32_t *__re
     }
 }
 
-// Edges in rank order: rank i -> (src, dst, relative t).
+// Edges in rank order, emitted as the incident entries of the next sort:
+// entry 2i+side of the edge of rank i sits at its source (side 0, direction
+// o) or destination (side 1, direction in), keyed by that centre and carrying
+// its timestamp, its neighbour and (rank << 1) | side.
 template <typename K>
-__global__ void k_rank_edges(const K *__restrict__ tkey, const uint64_t *__restrict__ sd,
-                             int64_t m, int32_t *__restrict__ esrc, int32_t *__restrict__ edst,
-                             int64_t *__restrict__ et) {
+__global__ void k_rank_entries(const K *__restrict__ tkey, const uint64_t *__restrict__ sd,
+                               int64_t m, uint32_t *__restrict__ keys,
+                               EntryPayload *__restrict__ vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t v = sd[i];
-        esrc[i] = (int32_t)(v >> 32);
-        edst[i] = (int32_t)(uint32_t)v;
-        et[i] = (int64_t)tkey[i];
-    }
-}
-
-// Incident entries in rank order, keyed by centre: entry 2i+side of edge rank i
-// is at its source (side 0, direction o) or destination (side 1, direction in),
-// carrying its timestamp and neighbour through the sort.
-__global__ void k_entry_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ edst,
-                             const int64_t *__restrict__ et, int64_t m,
-                             uint32_t *__restrict__ keys, EntryPayload *__restrict__ vals) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * m;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = j >> 1;
-        const int side = (int)(j & 1);
-        const uint32_t a = (uint32_t)esrc[i], b = (uint32_t)edst[i];
-        keys[j] = side ? b : a;
-        EntryPayload p;
-        p.t = et[i];
-        p.nbr = side ? a : b;
-        p.code = (uint32_t)j;  // (rank << 1) | side
-        vals[j] = p;
+        const uint32_t a = (uint32_t)(v >> 32), b = (uint32_t)v;
+        const int64_t t = (int64_t)tkey[i];
+        keys[2 * i] = a;
+        keys[2 * i + 1] = b;
+        vals[2 * i] = EntryPayload{t, b, (uint32_t)(2 * i)};
+        vals[2 * i + 1] = EntryPayload{t, a, (uint32_t)(2 * i + 1)};
     }
 }
 
@@ -130,33 +116,24 @@ __global__ void k_dir_flags(const EntryPayload *__restrict__ pl, int64_t n2,
         f[p] = (int32_t)(pl[p].code & 1u);
 }
 
-__global__ void k_fill_T(const uint32_t *__restrict__ centre, const EntryPayload *__restrict__ pl,
-                         const int32_t *__restrict__ cin, int64_t n2, TEnt *__restrict__ T,
-                         int64_t *__restrict__ tt, uint2 *__restrict__ tn,
-                         uint32_t *__restrict__ codes, int32_t *__restrict__ minflag) {
+__global__ void k_fill_entries(const uint32_t *__restrict__ centre,
+                               const EntryPayload *__restrict__ pl, int64_t n2,
+                               int64_t *__restrict__ tt, uint2 *__restrict__ tn,
+                               int32_t *__restrict__ tc, uint32_t *__restrict__ codes,
+                               int32_t *__restrict__ minflag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         const EntryPayload q = pl[p];
-        const int32_t rank = (int32_t)(q.code >> 1);
-        const int side = (int)(q.code & 1u);
         const uint32_t c = centre[p];
-        TEnt e;
-        e.t = q.t;
-        e.nbr = q.nbr | ((uint32_t)side << 31);
-        e.rank = rank;
-        e.cin = cin[p];
-        e.prev = -1;
-        e.next = -1;
-        e.centre = (int32_t)c;
-        T[p] = e;
-        tt[p] = e.t;
-        tn[p] = make_uint2(e.nbr, (uint32_t)rank);
+        tt[p] = q.t;
+        tn[p] = make_uint2(q.nbr | ((q.code & 1u) << 31), q.code >> 1);
+        tc[p] = (int32_t)c;
         codes[p] = q.code;
         minflag[p] = c < q.nbr ? 1 : 0;
     }
 }
 
-// pos_src / pos_dst[rank] = T position of the edge's entry at its source /
+// pos_src / pos_dst[rank] = position of the edge's entry at its source /
 // destination, for the ranks in [rlo, rhi) only. The build runs this once per
 // rank range whose part of the two arrays fits in L2, so the random 4-byte
 // stores merge in L2 instead of each costing a DRAM read-modify-write.
@@ -177,20 +154,21 @@ __global__ void k_pos_scatter(const uint32_t *__restrict__ codes, int64_t n2, ui
 // The entries at the smaller endpoint of each edge, keyed by the larger one.
 // In T order (centre, then rank); a stable sort by the key then yields every
 // node pair's edges as one run in rank order.
-__global__ void k_pair_compact(const TEnt *__restrict__ T, const int32_t *__restrict__ minflag,
-                               const int32_t *__restrict__ idx, int64_t n2,
-                               uint32_t *__restrict__ keys, PairPayload *__restrict__ vals) {
+__global__ void k_pair_compact(const uint2 *__restrict__ tn, const int32_t *__restrict__ tc,
+                               const int32_t *__restrict__ minflag, const int32_t *__restrict__ idx,
+                               int64_t n2, uint32_t *__restrict__ keys,
+                               PairPayload *__restrict__ vals) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (minflag[p]) {
-            const TEnt e = T[p];
+            const uint2 e = tn[p];
             const int32_t k = idx[p];
-            keys[k] = e.nbr & 0x7fffffffu;
+            keys[k] = e.x & 0x7fffffffu;
             PairPayload q;
             q.pos = (uint32_t)p;
-            q.centre = (uint32_t)e.centre;
-            q.rank = e.rank;
-            q.srcmin = (e.nbr >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
+            q.centre = (uint32_t)tc[p];
+            q.rank = (int32_t)e.y;
+            q.srcmin = (e.x >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
             vals[k] = q;
         }
     }
@@ -222,7 +200,7 @@ __global__ void k_pair_cum(const int32_t *__restrict__ cum, int64_t m, int2 *__r
 // at both of its nodes: link their entries.
 __global__ void k_links(const PairPayload *__restrict__ pp, const int32_t *__restrict__ head,
                         const int32_t *__restrict__ pos_src, const int32_t *__restrict__ pos_dst,
-                        int64_t m, TEnt *__restrict__ T) {
+                        int64_t m, int2 *__restrict__ lk) {
     for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (head[k]) continue;
@@ -230,10 +208,10 @@ __global__ void k_links(const PairPayload *__restrict__ pp, const int32_t *__res
         const int32_t cur0 = (int32_t)q.pos, prv0 = (int32_t)qp.pos;
         const int32_t cur1 = q.srcmin ? pos_dst[q.rank] : pos_src[q.rank];  // larger endpoint
         const int32_t prv1 = qp.srcmin ? pos_dst[qp.rank] : pos_src[qp.rank];
-        T[cur0].prev = prv0;
-        T[prv0].next = cur0;
-        T[cur1].prev = prv1;
-        T[prv1].next = cur1;
+        lk[cur0].x = prv0;
+        lk[prv0].y = cur0;
+        lk[cur1].x = prv1;
+        lk[prv1].y = cur1;
     }
 }
 
@@ -325,7 +303,7 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     exclusive_scan_i32(minflag, idx, n2, s);
     uint32_t *k1 = dev_alloc_n<uint32_t>(m, s), *k2 = dev_alloc_n<uint32_t>(m, s);
     PairPayload *v1 = dev_alloc_n<PairPayload>(m, s), *v2 = dev_alloc_n<PairPayload>(m, s);
-    TM_LAUNCH(k_pair_compact, grid_for(n2), 256, 0, s, g.T, minflag, idx, n2, k1, v1);
+    TM_LAUNCH(k_pair_compact, grid_for(n2), 256, 0, s, g.tn, g.tc, minflag, idx, n2, k1, v1);
     dev_free(idx, s);
     uint32_t *sk;
     PairPayload *sv;
@@ -340,7 +318,7 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, s, cum, m, g.pl);
     dev_free(cum, s);
     exclusive_scan_i32(head, run_id, m, s);
-    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pos_src, g.pos_dst, m, g.T);
+    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pos_src, g.pos_dst, m, g.lk);
     int32_t nruns = 0;
     TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     TM_CUDA(cudaStreamSynchronize(s));
@@ -391,9 +369,11 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     dev_free(v2, s);
 }
 
+// Sorts the edges by t - t_min (stable: ties keep the edge-id order) and
+// emits the 2m incident entries in rank order into (ekeys, evals).
 template <typename K>
 void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
-                  int keybits, int32_t *esrc, int32_t *edst, int64_t *et, cudaStream_t s) {
+                  int keybits, uint32_t *ekeys, EntryPayload *evals, cudaStream_t s) {
     const int64_t m = g.m;
     K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
     uint64_t *v1 = dev_alloc_n<uint64_t>(m, s), *v2 = dev_alloc_n<uint64_t>(m, s);
@@ -404,7 +384,7 @@ void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevG
         radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
     else
         radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-    TM_LAUNCH(k_rank_edges<K>, grid_for(m), 256, 0, s, sk, sv, m, esrc, edst, et);
+    TM_LAUNCH(k_rank_entries<K>, grid_for(m), 256, 0, s, sk, sv, m, ekeys, evals);
     dev_free(k1, s);
     dev_free(k2, s);
     dev_free(v1, s);
@@ -414,9 +394,11 @@ void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevG
 }  // namespace
 
 void free_graph(DevGraph &g, cudaStream_t s) {
-    dev_free(g.T, s);
     dev_free(g.tt, s);
     dev_free(g.tn, s);
+    dev_free(g.tc, s);
+    dev_free(g.cin, s);
+    dev_free(g.lk, s);
     dev_free(g.off, s);
     dev_free(g.pos_src, s);
     dev_free(g.pos_dst, s);
@@ -491,14 +473,17 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     }
 
     g.off = dev_alloc_n<int32_t>(n + 1, s);
-    g.T = dev_alloc_n<TEnt>(2 * m, s);
     g.tt = dev_alloc_n<int64_t>(2 * m, s);
     g.tn = dev_alloc_n<uint2>(2 * m, s);
+    g.tc = dev_alloc_n<int32_t>(2 * m, s);
+    g.cin = dev_alloc_n<int32_t>(2 * m + 1, s);
+    g.lk = dev_alloc_n<int2>(2 * m, s);
     g.pos_src = dev_alloc_n<int32_t>(m, s);
     g.pos_dst = dev_alloc_n<int32_t>(m, s);
     g.pl = dev_alloc_n<int2>(m + 1, s);
     if (m == 0) {
         TM_CUDA(cudaMemsetAsync(g.off, 0, sizeof(int32_t) * (n + 1), s));
+        TM_CUDA(cudaMemsetAsync(g.cin, 0, sizeof(int32_t), s));
         TM_CUDA(cudaMemsetAsync(g.pl, 0, sizeof(int2), s));
         g.hash = dev_alloc_n<PairSlot>(16, s);
         g.hash_mask = 15;
@@ -510,53 +495,46 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         return;
     }
 
-    // 2. rank order
-    int32_t *esrc = dev_alloc_n<int32_t>(m, s), *edst = dev_alloc_n<int32_t>(m, s);
-    int64_t *et = dev_alloc_n<int64_t>(m, s);
+    // 2. rank order, emitted as the incident entries
+    const int64_t n2 = 2 * m;
+    uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
+    EntryPayload *v1 = dev_alloc_n<EntryPayload>(n2, s), *v2 = dev_alloc_n<EntryPayload>(n2, s);
     const int keybits = bits_for(span);
     {
         PhaseTimer pt(TM_PH_TIME_SORT, s);
         if (keybits <= 32)
-            sort_by_time<uint32_t>(src, dst, t, g, keybits, esrc, edst, et, s);
+            sort_by_time<uint32_t>(src, dst, t, g, keybits, k1, v1, s);
         else
-            sort_by_time<uint64_t>(src, dst, t, g, keybits, esrc, edst, et, s);
+            sort_by_time<uint64_t>(src, dst, t, g, keybits, k1, v1, s);
         release_inputs();
     }
 
     // 3-4. S_u for every centre
-    const int64_t n2 = 2 * m;
     int32_t *minflag = dev_alloc_n<int32_t>(n2, s);
     {
         PhaseTimer pt(TM_PH_INCIDENT, s);
-        uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
-        EntryPayload *v1 = dev_alloc_n<EntryPayload>(n2, s), *v2 = dev_alloc_n<EntryPayload>(n2, s);
-        TM_LAUNCH(k_entry_keys, grid_for(n2), 256, 0, s, esrc, edst, et, m, k1, v1);
-        dev_free(et, s);
-        et = nullptr;
         uint32_t *sk;
         EntryPayload *sv;
         radix_sort_u32_ent(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
         TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, sk, n2, n, g.off);
-        int32_t *flags = dev_alloc_n<int32_t>(n2, s), *cin = dev_alloc_n<int32_t>(n2 + 1, s);
+        int32_t *flags = dev_alloc_n<int32_t>(n2, s);
         TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
-        exclusive_scan_i32(flags, cin, n2, s);
+        exclusive_scan_i32(flags, g.cin, n2, s);
         uint32_t *codes = reinterpret_cast<uint32_t *>(flags);  // flags are consumed by the scan
-        TM_LAUNCH(k_fill_T, grid_for(n2), 256, 0, s, sk, sv, cin, n2, g.T, g.tt, g.tn, codes,
+        TM_LAUNCH(k_fill_entries, grid_for(n2), 256, 0, s, sk, sv, n2, g.tt, g.tn, g.tc, codes,
                   minflag);
+        TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
         // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
         const int64_t ranks_per_pass = (int64_t)8 << 20;
         for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
             TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
                       (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);
         dev_free(flags, s);
-        dev_free(cin, s);
-        dev_free(k1, s);
-        dev_free(k2, s);
-        dev_free(v1, s);
-        dev_free(v2, s);
     }
-    dev_free(esrc, s);
-    dev_free(edst, s);
+    dev_free(k1, s);
+    dev_free(k2, s);
+    dev_free(v1, s);
+    dev_free(v2, s);
 
     // 5-6. pair list, hash, same-neighbour links
     {

@@ -3,9 +3,9 @@
 // the restatements are derived in the comments below.
 //
 // Notation for one centre u: S = S_u in (t, edge id) order, positions are
-// global indices into g.T; C_in(p) = inward entries before position p
-// (TEnt::cin, a global prefix, so only differences inside one centre are
-// used) and C_o(p) = p - C_in(p). For an entry r: W(r) = [lo(r), r), the
+// global entry indices; C_in(p) = inward entries before position p (g.cin, a
+// global prefix, so only differences inside one centre are used) and
+// C_o(p) = p - C_in(p). For an entry r: W(r) = [lo(r), r), the
 // earlier entries with t_r - t_p <= delta; F(r) = (r, hi(r)], the later
 // entries with t_q - t_r <= delta.
 //
@@ -151,36 +151,33 @@ __device__ __forceinline__ void flush_star_pair(const unsigned long long *sacc,
 }
 
 template <int D3>
-__device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
-                                                const int64_t *__restrict__ tt,
-                                                const int32_t *__restrict__ off, int64_t m2,
-                                                int64_t m, int64_t delta, int32_t r,
-                                                const TEnt &e, unsigned long long *sacc) {
-    const int64_t tr = e.t;
-    const int32_t u = e.centre;
-    const int32_t seg_b = off[u], seg_end = off[u + 1];
+__device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta, int32_t r,
+                                                int64_t tr, int32_t u, int2 lr,
+                                                unsigned long long *sacc) {
+    const int64_t *__restrict__ tt = g.tt;
+    const int32_t seg_b = g.off[u], seg_end = g.off[u + 1];
     // W(r) and F(r) bounds from the neighbouring entries of S_u (local reads);
     // the same-neighbour links are followed only when they land inside.
-    const bool wnd_back = e.prev >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
-    const bool wnd_fwd = e.next >= 0 && r + 1 < seg_end && tt[r + 1] - tr <= delta;
+    const bool wnd_back = lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
+    const bool wnd_fwd = lr.y >= 0 && r + 1 < seg_end && tt[r + 1] - tr <= delta;
     if (!wnd_back && !wnd_fwd) return;
-    const int64_t cin_end = seg_end < m2 ? (int64_t)T[seg_end].cin : m;
+    const int64_t cin_end = g.cin[seg_end];
+    const int64_t cin_r = g.cin[r];
     if (wnd_back) {
         const int32_t lo = gallop_lo(tt, seg_b, r, tr - delta);
-        if (e.prev >= lo) {
+        if (lr.x >= lo) {
             // per direction d of the run entries: n_d (count), c2s_{d,d'} (pairs),
             // X_{d,d'} (d' entries strictly between a and r), Y_{d,d'} (d' entries
             // before b, as a prefix); kept in scalars so they stay in registers
             uint64_t n0 = 0, n1 = 0, c00 = 0, c01 = 0, c10 = 0, c11 = 0;
             uint64_t X00 = 0, X01 = 0, X10 = 0, X11 = 0, Y00 = 0, Y01 = 0, Y10 = 0, Y11 = 0;
-            const int32_t cin_r = e.cin;
-            int32_t a = e.prev, cur = r;
+            int32_t a = lr.x, cur = r;
             while (a >= lo && a < cur) {  // links strictly decrease: the walk always ends
-                const TEnt ea = T[a];
-                const int da = dir_of(ea.nbr);
-                const uint64_t between_in = (uint64_t)((int64_t)cin_r - (ea.cin + da));
+                const int da = dir_of(g.tn[a].x);
+                const int64_t cin_a = g.cin[a];
+                const uint64_t between_in = (uint64_t)(cin_r - (cin_a + da));
                 const uint64_t between_o = (uint64_t)(r - a - 1) - between_in;
-                const uint64_t co_a = (uint64_t)(a - ea.cin), ci_a = (uint64_t)ea.cin;
+                const uint64_t co_a = (uint64_t)(a - cin_a), ci_a = (uint64_t)cin_a;
                 if (da) {  // pairs (a, later same-node entries in the window)
                     c10 += n0;
                     c11 += n1;
@@ -199,13 +196,13 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
                     Y01 += ci_a;
                 }
                 cur = a;
-                a = ea.prev;
+                a = g.lk[a].x;
             }
             const uint64_t n[2] = {n0, n1};
             const uint64_t c2s[2][2] = {{c00, c01}, {c10, c11}};
             const uint64_t X[2][2] = {{X00, X01}, {X10, X11}};
             const uint64_t Yp[2][2] = {{Y00, Y01}, {Y10, Y11}};
-            const int64_t cin_lo = T[lo].cin;
+            const int64_t cin_lo = g.cin[lo];
             const int64_t co_lo = (int64_t)lo - cin_lo;
 #pragma unroll
             for (int d1 = 0; d1 < 2; d1++)
@@ -230,20 +227,18 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
     }
     if (wnd_fwd) {
         const int32_t hi = gallop_hi(tt, r, seg_end, tr, delta);
-        if (e.next <= hi) {
+        if (lr.y <= hi) {
             // same-neighbour entries inside F(r): pairs leaving after hi(r)
             uint64_t f0 = 0, f1 = 0;
-            int32_t b = e.next, cur = r;
+            int32_t b = lr.y, cur = r;
             while (b > cur && b <= hi) {  // links strictly increase: the walk always ends
-                const TEnt eb = T[b];
-                if (dir_of(eb.nbr)) f1 += 1;
+                if (dir_of(g.tn[b].x)) f1 += 1;
                 else f0 += 1;
                 cur = b;
-                b = eb.next;
+                b = g.lk[b].y;
             }
             const uint64_t f[2] = {f0, f1};
-            const TEnt eh = T[hi];
-            const int64_t cin_h1 = (int64_t)eh.cin + dir_of(eh.nbr);  // C_in(hi+1)
+            const int64_t cin_h1 = (int64_t)g.cin[hi] + dir_of(g.tn[hi].x);  // C_in(hi+1)
             const int64_t after_in = cin_end - cin_h1;
             const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
 #pragma unroll
@@ -255,31 +250,29 @@ __device__ __forceinline__ void star_pair_entry(const TEnt *__restrict__ T,
     }
 }
 
-// Star/Pair contributions of the entries [begin, end) of g.T, visited by
-// threads tid, tid + nthreads, ...
-__device__ __forceinline__ void star_pair_range(const TEnt *__restrict__ T,
-                                                const int64_t *__restrict__ tt,
-                                                const int32_t *__restrict__ off, int64_t m,
-                                                int64_t delta, int64_t begin, int64_t end,
-                                                int64_t tid, int64_t nthreads,
+// Star/Pair contributions of the entries [begin, end), visited by threads
+// tid, tid + nthreads, ...
+__device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta, int64_t begin,
+                                                int64_t end, int64_t tid, int64_t nthreads,
                                                 unsigned long long *sacc) {
-    const int64_t m2 = 2 * m;
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
-        const TEnt e = T[r];
-        if (dir_of(e.nbr)) star_pair_entry<1>(T, tt, off, m2, m, delta, r, e, sacc);
-        else star_pair_entry<0>(T, tt, off, m2, m, delta, r, e, sacc);
+        const int64_t tr = g.tt[r];
+        const uint32_t nbr = g.tn[r].x;
+        const int32_t u = g.tc[r];
+        const int2 lr = g.lk[r];
+        if (dir_of(nbr)) star_pair_entry<1>(g, delta, r, tr, u, lr, sacc);
+        else star_pair_entry<0>(g, delta, r, tr, u, lr, sacc);
     }
 }
 
-__global__ void __launch_bounds__(THREADS)
-    k_star_pair(const TEnt *__restrict__ T, const int64_t *__restrict__ tt,
-                const int32_t *__restrict__ off, int64_t m, int64_t delta, int32_t begin,
-                int32_t end, unsigned long long *__restrict__ cells) {
+__global__ void __launch_bounds__(THREADS, 5)
+    k_star_pair(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
+                unsigned long long *__restrict__ cells) {
     __shared__ unsigned long long sacc[32];
     if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
     __syncthreads();
-    star_pair_range(T, tt, off, m, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+    star_pair_range(g, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                     (int64_t)gridDim.x * blockDim.x, sacc);
     __syncthreads();
     flush_star_pair(sacc, cells);
@@ -359,7 +352,7 @@ __device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int
 struct TriEdge {
     uint32_t u, w;
     int32_t rank_j;
-    int32_t small_lo;     // smaller window: T[small_lo, small_lo + work)
+    int32_t small_lo;     // smaller window: entries [small_lo, small_lo + work)
     int32_t work;
     int32_t rank_lo_big;  // rank of the first entry of the bigger window
     int32_t small_is_u;   // 1: the smaller window is W_u
@@ -424,35 +417,35 @@ constexpr int TRI_WARPS = THREADS / 32;
 // neighbour node counts both. The probes of the 32 edges of a warp are
 // flattened into one list that all lanes share, so a lane never waits for
 // another lane's long window.
-// Tri joins of the edges whose source entries lie in [begin, end) of g.T,
+// Tri joins of the edges whose source entries lie in [begin, end),
 // visited 32 entries at a time by warps wid, wid + nwarps, ...; `edges` and
 // `incl` are the calling warp's shared-memory staging (32 slots each).
 __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int64_t begin,
                                           int64_t end, int64_t wid, int64_t nwarps,
                                           TriEdge *edges, int32_t *incl,
                                           unsigned long long (&acc)[8]) {
-    const TEnt *__restrict__ T = g.T;
     const int lane = threadIdx.x & 31;
     for (int64_t base = begin + wid * 32; base < end; base += nwarps * 32) {
         const int64_t r = base + lane;
         TriEdge E;
         E.work = 0;
         if (r < end) {
-            const TEnt e = T[r];
-            if (dir_of(e.nbr) == 0) {
-                const uint32_t u = (uint32_t)e.centre;
+            const uint2 en = g.tn[r];
+            if (dir_of(en.x) == 0) {
+                const int64_t et = g.tt[r];
+                const uint32_t u = (uint32_t)g.tc[r];
                 const int32_t sb = g.off[u];
-                if (r > sb && e.t - g.tt[r - 1] <= delta) {
-                    const uint32_t w = node_of(e.nbr);
-                    const int32_t twin = g.pos_dst[e.rank];
+                if (r > sb && et - g.tt[r - 1] <= delta) {
+                    const uint32_t w = node_of(en.x);
+                    const int32_t twin = g.pos_dst[en.y];
                     const int32_t wb = g.off[w];
-                    if (twin > wb && e.t - g.tt[twin - 1] <= delta) {
-                        const int32_t lo_u = gallop_lo(g.tt, sb, (int32_t)r, e.t - delta);
-                        const int32_t lo_w = gallop_lo(g.tt, wb, twin, e.t - delta);
+                    if (twin > wb && et - g.tt[twin - 1] <= delta) {
+                        const int32_t lo_u = gallop_lo(g.tt, sb, (int32_t)r, et - delta);
+                        const int32_t lo_w = gallop_lo(g.tt, wb, twin, et - delta);
                         const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
                         E.u = u;
                         E.w = w;
-                        E.rank_j = e.rank;
+                        E.rank_j = (int32_t)en.y;
                         E.small_is_u = wu <= ww;
                         E.small_lo = E.small_is_u ? lo_u : lo_w;
                         E.work = E.small_is_u ? wu : ww;
@@ -517,29 +510,30 @@ __global__ void __launch_bounds__(THREADS)
     unsigned long long acc[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
-    const TEnt *__restrict__ T = g.T;
     for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = (int32_t)i;
-        const TEnt e = T[r];
-        const int dj = dir_of(e.nbr);
-        const uint32_t u = (uint32_t)e.centre, w = node_of(e.nbr);
-        const int32_t lo_u = gallop_lo(g.tt, g.off[u], r, e.t - delta);
+        const uint2 en = g.tn[r];
+        const int64_t et = g.tt[r];
+        const int dj = dir_of(en.x);
+        const uint32_t u = (uint32_t)g.tc[r], w = node_of(en.x);
+        const int32_t rank_j = (int32_t)en.y;
+        const int32_t lo_u = gallop_lo(g.tt, g.off[u], r, et - delta);
         if (lo_u == r) continue;
-        const int32_t twin = dj ? g.pos_src[e.rank] : g.pos_dst[e.rank];
-        const int32_t lo_w = gallop_lo(g.tt, g.off[w], twin, e.t - delta);
+        const int32_t twin = dj ? g.pos_src[rank_j] : g.pos_dst[rank_j];
+        const int32_t lo_w = gallop_lo(g.tt, g.off[w], twin, et - delta);
         if (lo_w == twin) continue;
-        const int32_t rank_lo_w = T[lo_w].rank;
+        const int32_t rank_lo_w = (int32_t)g.tn[lo_w].y;
         // items a of W_u, matches k of W_w ranked after a: centred at u
         for (int32_t a = lo_u; a < r; a++) {
-            const TEnt ea = T[a];
-            const uint32_t x = node_of(ea.nbr);
+            const uint2 ea = g.tn[a];
+            const uint32_t x = node_of(ea.x);
             if (x == w) continue;
             PairCounts c;
-            if (!pair_counts(g, pair_key(w, x), rank_lo_w, e.rank, ea.rank, c)) continue;
+            if (!pair_counts(g, pair_key(w, x), rank_lo_w, rank_j, (int32_t)ea.y, c)) continue;
             const int32_t from_x = x < w ? c.fa : c.na - c.fa;  // e_k = x -> w: o w.r.t. x
             const int32_t cnt = c.na;
-            const int di = dir_of(ea.nbr);
+            const int di = dir_of(ea.x);
             if (di) {
                 if (dj) { acc[IX(1, 1, 0)] += from_x; acc[IX(1, 1, 1)] += cnt - from_x; }
                 else { acc[IX(1, 0, 0)] += from_x; acc[IX(1, 0, 1)] += cnt - from_x; }
@@ -591,8 +585,7 @@ __global__ void __launch_bounds__(THREADS)
         if (it.kind == 0) {
             if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
             __syncthreads();
-            star_pair_range(g.T, g.tt, g.off, g.m, delta, it.begin, it.end, threadIdx.x, blockDim.x,
-                            sacc);
+            star_pair_range(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
             __syncthreads();
             flush_star_pair(sacc, cells);
         } else {
@@ -645,8 +638,7 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     if (blocks > cap) blocks = cap;
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, begin,
-                  end, dev_cells);
+        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
     }
     {
         PhaseTimer pt(TM_PH_TRI, s);
@@ -669,8 +661,7 @@ void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool t
     if (blocks > cap) blocks = cap;
     if (star_pair) {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, 0,
-                  (int32_t)n, dev_cells);
+        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     }
     if (tri) {
         PhaseTimer pt(TM_PH_TRI, s);
@@ -686,8 +677,7 @@ void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g.T, g.tt, g.off, g.m, delta, 0,
-              (int32_t)n, dev_cells);
+    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
 }

@@ -143,6 +143,20 @@ __device__ __forceinline__ int digit_of(K k, int shift) {
     return (int)((unsigned)(k >> shift) & (RADIX - 1));
 }
 
+// Lanes of the warp holding the same value d (9 bits: digits 0..255 and the
+// "no item" marker 256), from nine ballots: a lane keeps the lanes that agree
+// with it on every bit.
+__device__ __forceinline__ unsigned warp_peers9(int d) {
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const bool bit = (d >> b) & 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // Per-tile digit histogram: 128-bit loads, warp-private shared counters
 // (plain shared atomics; a skewed digit only contends inside one warp).
 template <typename K, int RS_ITEMS>
@@ -182,7 +196,7 @@ __global__ void __launch_bounds__(RS_THREADS)
 // counters into tile offsets; the tile is reordered in shared memory and
 // written out so that each digit's run goes to consecutive addresses.
 template <typename K, typename V>
-__global__ void __launch_bounds__(RS_THREADS)
+__global__ void __launch_bounds__(RS_THREADS, 4)
     k_radix_scatter(const K *__restrict__ keys_in, const V *__restrict__ vals_in,
                     K *__restrict__ keys_out, V *__restrict__ vals_out, int64_t n, int shift,
                     const int32_t *__restrict__ base_off, int64_t ntiles) {
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(RS_THREADS)
         key[r] = valid ? keys_in[tbase + li] : K(0);
         val[r] = valid ? vals_in[tbase + li] : V{};
         const int d = valid ? digit_of(key[r], shift) : RADIX;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = warp_peers9(d);
         const int before = d < RADIX ? cnt[warp * RADIX + d] : 0;
         __syncwarp();
         if (d < RADIX && lane == __ffs(peers) - 1) cnt[warp * RADIX + d] = before + __popc(peers);

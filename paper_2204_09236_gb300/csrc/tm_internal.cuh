@@ -65,19 +65,6 @@ int num_sms();
 
 // ------------------------------------------------------------ graph
 
-// One entry of a centre's time-sorted incident sequence S_u (Table 1 of the
-// paper: e = (t, v, dir) w.r.t. centre u), 32 bytes.
-struct TEnt {
-    int64_t t;       // timestamp minus the graph's smallest timestamp
-    uint32_t nbr;    // other endpoint v | dir << 31 (dir: 0 = o, 1 = in)
-    int32_t rank;    // position of the edge in the global (t, edge id) order
-    int32_t cin;     // inward entries before this one in the whole array
-    int32_t prev;    // previous entry of this centre with the same neighbour, or -1
-    int32_t next;    // next such entry, or -1
-    int32_t centre;  // u
-};
-static_assert(sizeof(TEnt) == 32, "TEnt must be 32 bytes");
-
 // Hash slot: unordered node pair -> its edge list E_(v,w) in the pair list.
 // A pair with a single edge keeps that edge in the slot itself:
 // begin = -(rank + 1), end = 1 if its source is the smaller id, else 0.
@@ -88,18 +75,23 @@ struct PairSlot {
 };
 constexpr uint64_t EMPTY_KEY = ~0ull;
 
+// The incident sequences S_u (Table 1: e = (t, v, dir) w.r.t. centre u) of
+// all centres, one after the other, each in (t, edge id) order; entry p of
+// the whole sequence is spread over the arrays below (structure of arrays,
+// 32 bytes per entry), so that every kernel reads only the fields it needs.
 struct DevGraph {
     int64_t m = 0;
     int32_t n = 0;
     int64_t tmin = 0;
-    TEnt *T = nullptr;          // 2m entries, grouped by centre, (t, id) order inside
-    // dense copies of two fields of T, for the window searches (tt: t) and
-    // the join items (tn: {nbr | dir << 31, rank}) of the counting kernels
-    int64_t *tt = nullptr;
-    uint2 *tn = nullptr;
-    int32_t *off = nullptr;     // n+1: S_u = T[off[u], off[u+1])
-    int32_t *pos_src = nullptr; // m, by rank: T position of the edge at its source
-    int32_t *pos_dst = nullptr; // m, by rank: T position at its destination
+    int64_t *tt = nullptr;      // 2m: t - t_min
+    uint2 *tn = nullptr;        // 2m: {other endpoint v | dir << 31 (0 = o, 1 = in), rank}
+    int32_t *tc = nullptr;      // 2m: centre u
+    int32_t *cin = nullptr;     // 2m+1: inward entries before p in the whole sequence
+    int2 *lk = nullptr;         // 2m: {previous, next} entry of the same centre and
+                                //     neighbour, or -1
+    int32_t *off = nullptr;     // n+1: S_u = entries [off[u], off[u+1])
+    int32_t *pos_src = nullptr; // m, by rank: entry of the edge at its source
+    int32_t *pos_dst = nullptr; // m, by rank: entry of the edge at its destination
     // pair list, m+1 entries: runs = E_(v,w) (grouped by node pair, ranks
     // ascending); .x = rank of the edge, .y = exclusive prefix over the list of
     // "source is the smaller id" (entry m holds the total).
@@ -159,7 +151,7 @@ struct EntryPayload {
     uint32_t nbr;   // the other endpoint
     uint32_t code;  // (rank << 1) | side, side 1 = at the destination (inward)
 };
-// Payload of an edge while the pair list is sorted: the T position of its
+// Payload of an edge while the pair list is sorted: the position of its
 // entry at the smaller endpoint, that endpoint, the edge's rank and whether
 // the smaller endpoint is its source.
 struct PairPayload {
@@ -195,7 +187,7 @@ void radix_sort_u64_v64(uint64_t *keys, uint64_t *vals, uint64_t *keys_tmp, uint
 // Number of 56 raw cells: Star[24] | Pair[8] | Tri[24].
 constexpr int NCELLS = 56;
 
-// Adds the counts of entries [begin, end) of g.T (as e3 for Star/Pair and as
+// Adds the counts of entries [begin, end) (as e3 for Star/Pair and as
 // e_j for Tri type II) into dev_cells (uint64[56], device). When
 // `tri_types_all` is set the Tri type-I/III cells are filled from type II by
 // the triangle rotation identity after the whole graph has been counted.
@@ -249,7 +241,7 @@ int current_device_id();
 }  // namespace tmi
 
 // The opaque handle of include/tm.h. A graph built from several component
-// graphs (tm_build_many) keeps where each component's entries start in T.
+// graphs (tm_build_many) keeps where each component's entries start.
 struct tm_graph {
     tmi::DevGraph g;
     int device = 0;
