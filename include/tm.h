@@ -238,6 +238,10 @@ int tm_server_poll(tm_server *s, int64_t id, uint64_t out[36], double *latency_m
 int tm_server_wait(tm_server *s, int64_t id, uint64_t out[36], double *latency_ms,
                    double timeout_s);
 int tm_server_stats(tm_server *s, tm_server_stats_t *st);
+/* The server's admission estimate for a graph of m edges and n nodes: the
+ * device bytes it holds while resident and the extra bytes its build needs
+ * at peak (a new graph is admitted when both fit in the budget). */
+int tm_estimate_bytes(int64_t m, int64_t n, int64_t *resident, int64_t *build_scratch);
 /* Keys of the resident graphs (up to cap written); returns how many there are. */
 int32_t tm_server_resident(tm_server *s, int64_t *keys, int32_t cap);
 /* Finishes the queued requests, stops the workers, frees every graph. */

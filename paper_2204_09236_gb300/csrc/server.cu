@@ -402,6 +402,13 @@ int tm_server_stats(tm_server *S, tm_server_stats_t *st) {
     return TM_OK;
 }
 
+int tm_estimate_bytes(int64_t m, int64_t n, int64_t *resident, int64_t *build_scratch) {
+    if (m < 0 || n < 0) return TM_EINVAL;
+    if (resident) *resident = resident_bytes(m, n);
+    if (build_scratch) *build_scratch = build_scratch_bytes(m);
+    return TM_OK;
+}
+
 int32_t tm_server_resident(tm_server *S, int64_t *keys, int32_t cap) {
     if (!S) return TM_EINVAL;
     std::lock_guard<std::mutex> lk(S->mu);

@@ -78,6 +78,7 @@ _lib.tm_server_stats.argtypes = [_P, ctypes.POINTER(_Stats)]
 _lib.tm_server_resident.restype = ctypes.c_int32
 _lib.tm_server_resident.argtypes = [_P, _P, ctypes.c_int32]
 _lib.tm_server_destroy.argtypes = [_P]
+_lib.tm_estimate_bytes.argtypes = [_i64, _i64, _P, _P]
 _lib.tm_profile_enable.argtypes = [ctypes.c_int]
 _lib.tm_profile_read.argtypes = [_P, _P]
 _lib.tm_last_error.restype = ctypes.c_char_p
@@ -332,6 +333,17 @@ def tm_tune_batch(g, deltas, reps=3):
     _check(_lib.tm_tune_batch(g.handle, d.ctypes.data_as(_P), int(reps), ctypes.byref(ie),
                               ctypes.byref(b), ctypes.byref(ms)))
     return ie.value, b.value, ms.value
+
+
+def tm_estimate_bytes(m, n):
+    """(resident bytes, build scratch bytes) of a graph, as the server admits it."""
+    r = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(_lib.tm_estimate_bytes(int(m), int(n), ctypes.byref(r), ctypes.byref(b)))
+    return r.value, b.value
+
+
+estimate_bytes = tm_estimate_bytes
 
 
 class Server:

@@ -78,12 +78,10 @@ def test_results_same_alone_and_in_the_mix(tm):
 
 def test_budget_admission_and_eviction(tm):
     graphs, deltas = pool(k=6, scale=0.2)
-    # the server's own estimate of one graph: resident arrays (<= 177 B/edge
-    # with the pair hash) + build scratch (96 B/edge) + 2 MiB; the budget
-    # holds one resident graph beside one build, so new graphs evict old ones
-    need = max(273 * len(g[0]) + 4 * (int(max(g[0].max(), g[1].max())) + 2) + (2 << 20)
-               for g in graphs)
-    budget = int(1.2 * need)
+    # the budget holds the largest graph resident beside one build, but not
+    # two resident graphs and a build: new graphs must evict old ones
+    est = [tm.estimate_bytes(len(g[0]), int(max(g[0].max(), g[1].max())) + 1) for g in graphs]
+    budget = int(1.2 * max(r + b for r, b in est))
     srv = tm.Server(budget_bytes=budget, workers=2, max_wave=4)
     ids = [(srv.submit(k, deltas[k], *graphs[k]), k) for k in range(len(graphs))]
     for rid, k in ids:
