@@ -524,8 +524,8 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         TM_LAUNCH(k_fill_entries, grid_for(n2), 256, 0, s, sk, sv, n2, g.tt, g.tn, g.tc, codes,
                   minflag);
         TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
-        // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
-        const int64_t ranks_per_pass = (int64_t)8 << 20;
+        // both position arrays take 8 bytes per rank: at most 96 MB of them per pass
+        const int64_t ranks_per_pass = (int64_t)12 << 20;
         for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
             TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
                       (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);

@@ -318,11 +318,9 @@ __device__ __forceinline__ uint64_t load_keep(const uint64_t *p) {
     return v;
 }
 
-__device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int32_t rank_lo,
-                                            int32_t rank_hi, int32_t at, PairCounts &c) {
-    uint32_t word;
-    const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
-    if ((load_keep(g.bloom + word) & bits) != bits) return false;  // the pair never met
+// As pair_counts, for a pair that passed the Bloom filter.
+__device__ __forceinline__ bool pair_counts_hashed(const DevGraph &g, uint64_t key, int32_t rank_lo,
+                                                   int32_t rank_hi, int32_t at, PairCounts &c) {
     const int2 run = find_pair(g.hash, g.hash_mask, key);
     if (run.x < 0) {  // single edge kept in the slot
         const int32_t r1 = -run.x - 1;
@@ -347,6 +345,14 @@ __device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int
     return true;
 }
 
+__device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int32_t rank_lo,
+                                            int32_t rank_hi, int32_t at, PairCounts &c) {
+    uint32_t word;
+    const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
+    if ((load_keep(g.bloom + word) & bits) != bits) return false;  // the pair never met
+    return pair_counts_hashed(g, key, rank_lo, rank_hi, at, c);
+}
+
 // The join of one edge e_j = u -> w (u its source): the smaller of the two
 // endpoint windows is enumerated, the matches are looked up in the other.
 struct TriEdge {
@@ -363,13 +369,13 @@ struct TriEdge {
 // (dj = 0); at the destination w it is inward (dj = 1). A match ranked after
 // the item is centred at the item's centre, one ranked before it at the big
 // window's centre.
-__device__ __forceinline__ void tri_probe(const DevGraph &g, const TriEdge &E, const uint2 it,
-                                          unsigned long long (&acc)[8]) {
+__device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, const TriEdge &E,
+                                                 const uint2 it, uint64_t key,
+                                                 unsigned long long (&acc)[8]) {
     const uint32_t x = node_of(it.x);
     const uint32_t big = E.small_is_u ? E.w : E.u;
-    if (x == big) return;  // an edge of the pair (u, w) itself
     PairCounts c;
-    if (!pair_counts(g, pair_key(big, x), E.rank_lo_big, E.rank_j, (int32_t)it.y, c)) return;
+    if (!pair_counts_hashed(g, key, E.rank_lo_big, E.rank_j, (int32_t)it.y, c)) return;
     // a big-side edge big -> x is outward at big and inward at x
     const bool big_is_min = big < x;
     const int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
@@ -462,18 +468,24 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
         __syncwarp();
         for (int32_t jb = 0; jb < total; jb += 32) {
             const int32_t j = jb + lane;
-            if (j < total) {
-                // owner: the first lane whose inclusive prefix exceeds j
-                int lo = 0, hi = 31;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (incl[mid] > j) hi = mid;
-                    else lo = mid + 1;
-                }
-                const TriEdge &B = edges[lo];
-                const int32_t k = j - (incl[lo] - B.work);
-                tri_probe(g, B, g.tn[B.small_lo + k], acc);
+            if (j >= total) continue;
+            // owner: the first lane whose inclusive prefix exceeds j
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (incl[mid] > j) hi = mid;
+                else lo = mid + 1;
             }
+            const TriEdge &B = edges[lo];
+            const uint2 it = g.tn[B.small_lo + (j - (incl[lo] - B.work))];
+            const uint32_t x = node_of(it.x);
+            const uint32_t big = B.small_is_u ? B.w : B.u;
+            if (x == big) continue;  // an edge of the pair (u, w) itself
+            const uint64_t key = pair_key(big, x);
+            uint32_t word;
+            const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
+            if ((load_keep(g.bloom + word) & bits) != bits) continue;  // the pair never met
+            tri_probe_hashed(g, B, it, key, acc);
         }
         __syncwarp();
     }

@@ -227,11 +227,11 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
         val[r] = valid ? vals_in[tbase + li] : V{};
         const int d = valid ? digit_of(key[r], shift) : RADIX;
         const unsigned peers = warp_peers9(d);
-        const int before = d < RADIX ? cnt[warp * RADIX + d] : 0;
-        __syncwarp();
-        if (d < RADIX && lane == __ffs(peers) - 1) cnt[warp * RADIX + d] = before + __popc(peers);
-        __syncwarp();
-        rnk[r] = before + __popc(peers & lt_mask);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (d < RADIX && lane == leader) base = atomicAdd(&cnt[warp * RADIX + d], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        rnk[r] = base + __popc(peers & lt_mask);
     }
     __syncthreads();
     {
