@@ -43,7 +43,7 @@ ALGO_BYTES = {"star_pair": 32, "tri": 48, "time_sort": 16, "incident": 48, "pair
 # DRAM bytes (read + write) of one k_tri launch on the full workload, from one
 # ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
 # (profiles/k_tri_k_star_pair_dram_large_60M.md); None until captured for the current kernel
-TRI_TRAFFIC = {"large": 24.57e9 + 0.105e9}
+TRI_TRAFFIC = {}
 
 WORKLOADS = {
     "large": dict(desc="large: 2.5M nodes, 60M edges, Zipf(2.0) degree law, out-degree cap 2e5, "

@@ -150,22 +150,24 @@ __device__ __forceinline__ void flush_star_pair(const unsigned long long *sacc,
     }
 }
 
-template <int D3>
+// LO: lo_r = lo(r) comes from k_window_lo; otherwise it is found here.
+template <int D3, bool LO>
 __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta, int32_t r,
-                                                int64_t tr, int32_t u, int2 lr,
+                                                int64_t tr, int32_t u, int2 lr, int32_t lo_r,
                                                 unsigned long long *sacc) {
     const int64_t *__restrict__ tt = g.tt;
     const int32_t seg_b = g.off[u], seg_end = g.off[u + 1];
     // W(r) and F(r) bounds from the neighbouring entries of S_u (local reads);
     // the same-neighbour links are followed only when they land inside.
-    const bool wnd_back = lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
+    const bool wnd_back =
+        LO ? lr.x >= lo_r : lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
     const bool wnd_fwd = lr.y >= 0 && r + 1 < seg_end && tt[r + 1] - tr <= delta;
     if (!wnd_back && !wnd_fwd) return;
     const int64_t cin_end = g.cin[seg_end];
     const int64_t cin_r = g.cin[r];
     if (wnd_back) {
-        const int32_t lo = gallop_lo(tt, seg_b, r, tr - delta);
-        if (lr.x >= lo) {
+        const int32_t lo = LO ? lo_r : gallop_lo(tt, seg_b, r, tr - delta);
+        if (LO || lr.x >= lo) {
             // per direction d of the run entries: n_d (count), c2s_{d,d'} (pairs),
             // X_{d,d'} (d' entries strictly between a and r), Y_{d,d'} (d' entries
             // before b, as a prefix); kept in scalars so they stay in registers
@@ -251,9 +253,11 @@ __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta
 }
 
 // Star/Pair contributions of the entries [begin, end), visited by threads
-// tid, tid + nthreads, ...
+// tid, tid + nthreads, ...; with LO the window starts are read from wlo.
+template <bool LO>
 __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta, int64_t begin,
                                                 int64_t end, int64_t tid, int64_t nthreads,
+                                                const int32_t *__restrict__ wlo,
                                                 unsigned long long *sacc) {
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
@@ -261,19 +265,38 @@ __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta
         const uint32_t nbr = g.tn[r].x;
         const int32_t u = g.tc[r];
         const int2 lr = g.lk[r];
-        if (dir_of(nbr)) star_pair_entry<1>(g, delta, r, tr, u, lr, sacc);
-        else star_pair_entry<0>(g, delta, r, tr, u, lr, sacc);
+        const int32_t lo_r = LO ? wlo[r] : 0;
+        if (dir_of(nbr)) star_pair_entry<1, LO>(g, delta, r, tr, u, lr, lo_r, sacc);
+        else star_pair_entry<0, LO>(g, delta, r, tr, u, lr, lo_r, sacc);
     }
 }
 
+// lo(r) for every entry r in [begin, end): the first entry of W(r), r itself
+// when the window is empty. Consecutive entries share their centre and most of
+// their window, so the backward searches of a warp read the same lines.
+__global__ void __launch_bounds__(THREADS)
+    k_window_lo(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
+                int32_t *__restrict__ wlo) {
+    for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = (int32_t)i;
+        const int64_t tr = g.tt[r];
+        const int32_t sb = g.off[g.tc[r]];
+        int32_t lo = r;
+        if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
+        wlo[r] = lo;
+    }
+}
+
+template <bool LO>
 __global__ void __launch_bounds__(THREADS, 5)
     k_star_pair(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-                unsigned long long *__restrict__ cells) {
+                const int32_t *__restrict__ wlo, unsigned long long *__restrict__ cells) {
     __shared__ unsigned long long sacc[32];
     if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
     __syncthreads();
-    star_pair_range(g, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                    (int64_t)gridDim.x * blockDim.x, sacc);
+    star_pair_range<LO>(g, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x, wlo, sacc);
     __syncthreads();
     flush_star_pair(sacc, cells);
 }
@@ -426,16 +449,36 @@ constexpr int TRI_WARPS = THREADS / 32;
 // Tri joins of the edges whose source entries lie in [begin, end),
 // visited 32 entries at a time by warps wid, wid + nwarps, ...; `edges` and
 // `incl` are the calling warp's shared-memory staging (32 slots each).
+// With LO the window starts are read from wlo (k_window_lo) instead of being
+// searched for.
+template <bool LO>
 __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int64_t begin,
                                           int64_t end, int64_t wid, int64_t nwarps,
-                                          TriEdge *edges, int32_t *incl,
-                                          unsigned long long (&acc)[8]) {
+                                          const int32_t *__restrict__ wlo, TriEdge *edges,
+                                          int32_t *incl, unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = begin + wid * 32; base < end; base += nwarps * 32) {
         const int64_t r = base + lane;
         TriEdge E;
         E.work = 0;
-        if (r < end) {
+        if (LO && r < end) {
+            const uint2 en = g.tn[r];
+            const int32_t lo_u = wlo[r];
+            if (dir_of(en.x) == 0 && lo_u < r) {
+                const int32_t twin = g.pos_dst[en.y];
+                const int32_t lo_w = wlo[twin];
+                if (lo_w < twin) {
+                    const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
+                    E.u = (uint32_t)g.tc[r];
+                    E.w = node_of(en.x);
+                    E.rank_j = (int32_t)en.y;
+                    E.small_is_u = wu <= ww;
+                    E.small_lo = E.small_is_u ? lo_u : lo_w;
+                    E.work = E.small_is_u ? wu : ww;
+                    E.rank_lo_big = (int32_t)g.tn[E.small_is_u ? lo_w : lo_u].y;
+                }
+            }
+        } else if (!LO && r < end) {
             const uint2 en = g.tn[r];
             if (dir_of(en.x) == 0) {
                 const int64_t et = g.tt[r];
@@ -498,17 +541,18 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
 // neighbour node counts both. The probes of the 32 edges of a warp are
 // flattened into one list that all lanes share, so a lane never waits for
 // another lane's long window.
+template <bool LO>
 __global__ void __launch_bounds__(THREADS)
     k_tri(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-          unsigned long long *__restrict__ cells) {
+          const int32_t *__restrict__ wlo, unsigned long long *__restrict__ cells) {
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
     unsigned long long acc[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
     const int warp = threadIdx.x >> 5;
-    tri_range(g, delta, begin, end, blockIdx.x * (int64_t)TRI_WARPS + warp,
-              (int64_t)gridDim.x * TRI_WARPS, edges[warp], incl[warp], acc);
+    tri_range<LO>(g, delta, begin, end, blockIdx.x * (int64_t)TRI_WARPS + warp,
+                  (int64_t)gridDim.x * TRI_WARPS, wlo, edges[warp], incl[warp], acc);
     // type II lives at Tri cells 8..15 (T = 1)
     block_flush<8, 0>(acc, 32 + 8, cells);
 }
@@ -597,14 +641,16 @@ __global__ void __launch_bounds__(THREADS)
         if (it.kind == 0) {
             if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
             __syncthreads();
-            star_pair_range(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
+            star_pair_range<false>(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, nullptr,
+                                   sacc);
             __syncthreads();
             flush_star_pair(sacc, cells);
         } else {
             unsigned long long acc[8];
 #pragma unroll
             for (int c = 0; c < 8; c++) acc[c] = 0;
-            tri_range(g, delta, it.begin, it.end, warp, TRI_WARPS, edges[warp], incl[warp], acc);
+            tri_range<false>(g, delta, it.begin, it.end, warp, TRI_WARPS, nullptr, edges[warp],
+                             incl[warp], acc);
             block_flush<8, 0>(acc, 32 + 8, cells);
         }
     }
@@ -648,38 +694,44 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
+    if (begin == 0 && end == 2 * g.m) {
+        launch_count_parts(g, delta, true, true, dev_cells, s, false);
+        return;
+    }
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
+        TM_LAUNCH(k_star_pair<false>, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end,
+                  nullptr, dev_cells);
     }
     {
         PhaseTimer pt(TM_PH_TRI, s);
-        if (begin == 0 && end == 2 * g.m) {
-            // whole graph: each edge once, at its source entry
-            TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
-        } else {
-            TM_LAUNCH(k_tri_centre, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end,
-                      dev_cells);
-        }
+        TM_LAUNCH(k_tri_centre, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
     }
 }
 
 void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,
-                        unsigned long long *dev_cells, cudaStream_t s) {
+                        unsigned long long *dev_cells, cudaStream_t s, bool fill) {
     const int64_t n = 2 * g.m;
     if (n == 0) return;
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    if (star_pair) {
+    // the window start of every entry, found once for both sweeps
+    int32_t *wlo = dev_alloc_n<int32_t>(n, s);
+    {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
+        TM_LAUNCH(k_window_lo, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo);
+        if (star_pair)
+            TM_LAUNCH(k_star_pair<true>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n,
+                      wlo, dev_cells);
     }
     if (tri) {
         PhaseTimer pt(TM_PH_TRI, s);
-        TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
-        TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
+        TM_LAUNCH(k_tri<true>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo,
+                  dev_cells);
+        if (fill) TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
     }
+    dev_free(wlo, s);
 }
 
 void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,
@@ -689,8 +741,10 @@ void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
-    TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
+    TM_LAUNCH(k_star_pair<false>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n,
+              nullptr, dev_cells);
+    TM_LAUNCH(k_tri<false>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, nullptr,
+              dev_cells);
     TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
 }
 

@@ -195,9 +195,10 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
                   unsigned long long *dev_cells, cudaStream_t s);
 void launch_fill_tri_types(unsigned long long *dev_cells, cudaStream_t s);
 
-// Only the Star/Pair kernel and/or only the Tri kernel (with its type fill).
+// Only the Star/Pair kernel and/or only the Tri kernel (with its type fill
+// unless fill is false), after the window-start pass both of them read.
 void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,
-                        unsigned long long *dev_cells, cudaStream_t s);
+                        unsigned long long *dev_cells, cudaStream_t s, bool fill = true);
 
 // The whole-graph count (Star/Pair, Tri, type-I/III fill) into dev_cells with
 // no phase timers and no allocation of any kind.
