@@ -14,7 +14,7 @@
 #include <cstring>
 #include <vector>
 
-#include "tm_internal.cuh"
+#include "radix.cuh"
 
 namespace tmi {
 
@@ -78,25 +78,44 @@ __global__ void k_time_keys(const int32_t *__restrict__ src, const int32_t *__re
     }
 }
 
-// Edges in rank order, emitted as the incident entries of the next sort:
-// entry 2i+side of the edge of rank i sits at its source (side 0, direction
-// o) or destination (side 1, direction in), keyed by that centre and carrying
-// its timestamp, its neighbour and (rank << 1) | side.
-template <typename K>
-__global__ void k_rank_entries(const K *__restrict__ tkey, const uint64_t *__restrict__ sd,
-                               int64_t m, uint32_t *__restrict__ keys,
-                               EntryPayload *__restrict__ vals) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t v = sd[i];
-        const uint32_t a = (uint32_t)(v >> 32), b = (uint32_t)v;
-        const int64_t t = (int64_t)tkey[i];
-        keys[2 * i] = a;
-        keys[2 * i + 1] = b;
-        vals[2 * i] = EntryPayload{t, b, (uint32_t)(2 * i)};
-        vals[2 * i + 1] = EntryPayload{t, a, (uint32_t)(2 * i + 1)};
+// The incident entries, generated from the edges in rank order as the first
+// pass of their sort by centre reads them: entry i = 2 * rank + side of the
+// edge of that rank sits at its source (side 0, direction o) or destination
+// (side 1, direction in), keyed by that centre and carrying its timestamp, its
+// neighbour and (rank << 1) | side.
+template <typename TK>
+struct EntryGen {
+    static constexpr bool VEC_KEYS = false;
+    const TK *__restrict__ tkey;      // t - t_min in rank order
+    const uint64_t *__restrict__ sd;  // (src << 32) | dst in rank order
+    __device__ __forceinline__ uint32_t key(int64_t i) const {
+        const uint64_t v = sd[i >> 1];
+        return (i & 1) ? (uint32_t)v : (uint32_t)(v >> 32);
     }
-}
+    __device__ __forceinline__ EntryPayload val(int64_t i) const {
+        const uint64_t v = sd[i >> 1];
+        const uint32_t other = (i & 1) ? (uint32_t)(v >> 32) : (uint32_t)v;
+        return EntryPayload{(int64_t)tkey[i >> 1], other, (uint32_t)i};
+    }
+};
+
+// The last pass of the centre sort writes every entry in its final form: the
+// entry arrays, its code (rank << 1 | side) for the position scatter and the
+// in-prefix, and whether its centre is the smaller endpoint.
+struct EntryStore {
+    int64_t *__restrict__ tt;
+    uint2 *__restrict__ tn;
+    int32_t *__restrict__ tc;
+    uint32_t *__restrict__ codes;
+    int32_t *__restrict__ minflag;
+    __device__ __forceinline__ void store(int64_t p, uint32_t c, const EntryPayload &q) const {
+        tt[p] = q.t;
+        tn[p] = make_uint2(q.nbr | ((q.code & 1u) << 31), q.code >> 1);
+        tc[p] = (int32_t)c;
+        codes[p] = q.code;
+        minflag[p] = c < q.nbr ? 1 : 0;
+    }
+};
 
 // off[u] = first position of centre u in the centre-sorted entries.
 __global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64_t n,
@@ -106,30 +125,6 @@ __global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64
         const int64_t lo = p == 0 ? 0 : (int64_t)centre[p - 1] + 1;
         const int64_t hi = p == n2 ? n : (int64_t)centre[p];
         for (int64_t u = lo; u <= hi; u++) off[u] = (int32_t)p;
-    }
-}
-
-__global__ void k_dir_flags(const EntryPayload *__restrict__ pl, int64_t n2,
-                            int32_t *__restrict__ f) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
-         p += (int64_t)gridDim.x * blockDim.x)
-        f[p] = (int32_t)(pl[p].code & 1u);
-}
-
-__global__ void k_fill_entries(const uint32_t *__restrict__ centre,
-                               const EntryPayload *__restrict__ pl, int64_t n2,
-                               int64_t *__restrict__ tt, uint2 *__restrict__ tn,
-                               int32_t *__restrict__ tc, uint32_t *__restrict__ codes,
-                               int32_t *__restrict__ minflag) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const EntryPayload q = pl[p];
-        const uint32_t c = centre[p];
-        tt[p] = q.t;
-        tn[p] = make_uint2(q.nbr | ((q.code & 1u) << 31), q.code >> 1);
-        tc[p] = (int32_t)c;
-        codes[p] = q.code;
-        minflag[p] = c < q.nbr ? 1 : 0;
     }
 }
 
@@ -369,26 +364,80 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
     dev_free(v2, s);
 }
 
-// Sorts the edges by t - t_min (stable: ties keep the edge-id order) and
-// emits the 2m incident entries in rank order into (ekeys, evals).
-template <typename K>
-void sort_by_time(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
-                  int keybits, uint32_t *ekeys, EntryPayload *evals, cudaStream_t s) {
-    const int64_t m = g.m;
-    K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
-    uint64_t *v1 = dev_alloc_n<uint64_t>(m, s), *v2 = dev_alloc_n<uint64_t>(m, s);
-    TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin, k1, v1);
+// Sorts the edges by t - t_min (stable: ties keep the edge-id order), then
+// sorts their 2m incident entries by centre (stable: each S_u stays in rank
+// order): the first pass of the second sort generates the entries from the
+// rank-ordered edges, its last pass writes the entry arrays of g, the entry
+// codes and minflag. Then off, cin and the position arrays. Scratch buffers
+// (and, through release_inputs, the edge arrays) are released as soon as the
+// kernels after them no longer read them.
+template <typename K, typename Release>
+void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
+                            int keybits, int nbits, int32_t *minflag, Release release_inputs,
+                            cudaStream_t s) {
+    const int64_t m = g.m, n2 = 2 * m, n = g.n;
     K *sk;
     uint64_t *sv;
-    if constexpr (sizeof(K) == 4)
-        radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-    else
-        radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-    TM_LAUNCH(k_rank_entries<K>, grid_for(m), 256, 0, s, sk, sv, m, ekeys, evals);
-    dev_free(k1, s);
-    dev_free(k2, s);
-    dev_free(v1, s);
-    dev_free(v2, s);
+    K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
+    uint64_t *v1 = dev_alloc_n<uint64_t>(m, s), *v2 = dev_alloc_n<uint64_t>(m, s);
+    {
+        PhaseTimer pt(TM_PH_TIME_SORT, s);
+        TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin, k1,
+                  v1);
+        release_inputs();
+        if constexpr (sizeof(K) == 4)
+            radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+        else
+            radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+        // the pair not holding the result is free now
+        dev_free(sk == k1 ? k2 : k1, s);
+        dev_free(sv == v1 ? v2 : v1, s);
+    }
+    PhaseTimer pt(TM_PH_INCIDENT, s);
+    uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);
+    using V = EntryPayload;
+    using radix::ArrayIn;
+    using radix::ArrayOut;
+    const EntryGen<K> gen{sk, sv};
+    const EntryStore out{g.tt, g.tn, g.tc, codes, minflag};
+    const int passes = nbits > 8 ? (nbits + 7) / 8 : 1;
+    const int64_t ntiles = (n2 + radix::Cfg<uint32_t, V>::TILE - 1) / radix::Cfg<uint32_t, V>::TILE;
+    int32_t *hist = dev_alloc_n<int32_t>(radix::RADIX * ntiles + 1, s);
+    if (passes == 1) {
+        radix::pass<uint32_t, V>(gen, out, n2, 0, hist, s);
+        dev_free(sk, s);
+        dev_free(sv, s);
+    } else {
+        uint32_t *ka = dev_alloc_n<uint32_t>(n2, s);
+        V *va = dev_alloc_n<V>(n2, s);
+        radix::pass<uint32_t, V>(gen, ArrayOut<uint32_t, V>{ka, va}, n2, 0, hist, s);
+        dev_free(sk, s);
+        dev_free(sv, s);
+        for (int p = 1; p + 1 < passes; p++) {
+            uint32_t *kb = dev_alloc_n<uint32_t>(n2, s);
+            V *vb = dev_alloc_n<V>(n2, s);
+            radix::pass<uint32_t, V>(ArrayIn<uint32_t, V>{ka, va}, ArrayOut<uint32_t, V>{kb, vb}, n2,
+                                     8 * p, hist, s);
+            dev_free(ka, s);
+            dev_free(va, s);
+            ka = kb;
+            va = vb;
+        }
+        radix::pass<uint32_t, V>(ArrayIn<uint32_t, V>{ka, va}, out, n2, 8 * (passes - 1), hist, s);
+        dev_free(ka, s);
+        dev_free(va, s);
+    }
+    dev_free(hist, s);
+    TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, reinterpret_cast<const uint32_t *>(g.tc), n2,
+              n, g.off);
+    exclusive_scan_low_bit(codes, g.cin, n2, s);
+    TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
+    // both position arrays take 8 bytes per rank: at most 96 MB of them per pass
+    const int64_t ranks_per_pass = (int64_t)12 << 20;
+    for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
+        TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
+                  (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);
+    dev_free(codes, s);
 }
 
 }  // namespace
@@ -495,46 +544,14 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
         return;
     }
 
-    // 2. rank order, emitted as the incident entries
-    const int64_t n2 = 2 * m;
-    uint32_t *k1 = dev_alloc_n<uint32_t>(n2, s), *k2 = dev_alloc_n<uint32_t>(n2, s);
-    EntryPayload *v1 = dev_alloc_n<EntryPayload>(n2, s), *v2 = dev_alloc_n<EntryPayload>(n2, s);
+    // 2-4. rank order, then S_u for every centre
     const int keybits = bits_for(span);
-    {
-        PhaseTimer pt(TM_PH_TIME_SORT, s);
-        if (keybits <= 32)
-            sort_by_time<uint32_t>(src, dst, t, g, keybits, k1, v1, s);
-        else
-            sort_by_time<uint64_t>(src, dst, t, g, keybits, k1, v1, s);
-        release_inputs();
-    }
-
-    // 3-4. S_u for every centre
-    int32_t *minflag = dev_alloc_n<int32_t>(n2, s);
-    {
-        PhaseTimer pt(TM_PH_INCIDENT, s);
-        uint32_t *sk;
-        EntryPayload *sv;
-        radix_sort_u32_ent(k1, v1, k2, v2, n2, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
-        TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, sk, n2, n, g.off);
-        int32_t *flags = dev_alloc_n<int32_t>(n2, s);
-        TM_LAUNCH(k_dir_flags, grid_for(n2), 256, 0, s, sv, n2, flags);
-        exclusive_scan_i32(flags, g.cin, n2, s);
-        uint32_t *codes = reinterpret_cast<uint32_t *>(flags);  // flags are consumed by the scan
-        TM_LAUNCH(k_fill_entries, grid_for(n2), 256, 0, s, sk, sv, n2, g.tt, g.tn, g.tc, codes,
-                  minflag);
-        TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
-        // both position arrays take 8 bytes per rank: at most 96 MB of them per pass
-        const int64_t ranks_per_pass = (int64_t)12 << 20;
-        for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
-            TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
-                      (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);
-        dev_free(flags, s);
-    }
-    dev_free(k1, s);
-    dev_free(k2, s);
-    dev_free(v1, s);
-    dev_free(v2, s);
+    const int nbits = bits_for((uint64_t)(n - 1));
+    int32_t *minflag = dev_alloc_n<int32_t>(2 * m, s);
+    if (keybits <= 32)
+        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, minflag, release_inputs, s);
+    else
+        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, minflag, release_inputs, s);
 
     // 5-6. pair list, hash, same-neighbour links
     {

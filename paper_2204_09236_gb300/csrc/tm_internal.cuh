@@ -133,17 +133,15 @@ __host__ __device__ inline uint32_t hash_pair(uint64_t k) {
 // Exclusive prefix sum: out[i] = sum(in[0..i)), out[n] = total (out has n+1
 // elements; out == in is allowed when in also has n+1 elements); n >= 0.
 void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+// The same over the low bit of each element of `in`.
+void exclusive_scan_low_bit(const uint32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 // Sorts `keys`/`vals` of length n using the given scratch buffers of the same
 // length; on return the sorted data is in (*keys_out, *vals_out), which is
-// either the input or the scratch pair.
-void radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp,
-                    int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
-                    uint32_t **vals_out);
-void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
-                    int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
-                    uint32_t **vals_out);
+// either the input or the scratch pair. Key buffers must be 16-byte aligned.
+// (Sorts whose first pass generates its items, or whose last pass writes them
+// in another form, use the kernels of radix.cuh directly.)
 // Payload of an incident entry while it is sorted by centre: everything its
 // S_u entry needs, so the entry is written without gathers afterwards.
 struct EntryPayload {
@@ -172,9 +170,6 @@ void radix_sort_u32_rec(uint32_t *keys, HashRecord *vals, uint32_t *keys_tmp, Ha
 void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
                          PairPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
                          uint32_t **keys_out, PairPayload **vals_out);
-void radix_sort_u32_ent(uint32_t *keys, EntryPayload *vals, uint32_t *keys_tmp,
-                        EntryPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
-                        uint32_t **keys_out, EntryPayload **vals_out);
 void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
                         int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
                         uint64_t **vals_out);
