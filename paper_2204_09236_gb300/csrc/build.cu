@@ -88,6 +88,7 @@ struct EntryGen {
     static constexpr bool VEC_KEYS = false;
     const TK *__restrict__ tkey;      // t - t_min in rank order
     const uint64_t *__restrict__ sd;  // (src << 32) | dst in rank order
+    __device__ __forceinline__ bool valid(int64_t) const { return true; }
     __device__ __forceinline__ uint32_t key(int64_t i) const {
         const uint64_t v = sd[i >> 1];
         return (i & 1) ? (uint32_t)v : (uint32_t)(v >> 32);
@@ -100,20 +101,41 @@ struct EntryGen {
 };
 
 // The last pass of the centre sort writes every entry in its final form: the
-// entry arrays, its code (rank << 1 | side) for the position scatter and the
-// in-prefix, and whether its centre is the smaller endpoint.
+// entry arrays and its code (rank << 1 | side) for the position scatter and
+// the in-prefix.
 struct EntryStore {
     int64_t *__restrict__ tt;
     uint2 *__restrict__ tn;
     int32_t *__restrict__ tc;
     uint32_t *__restrict__ codes;
-    int32_t *__restrict__ minflag;
     __device__ __forceinline__ void store(int64_t p, uint32_t c, const EntryPayload &q) const {
         tt[p] = q.t;
         tn[p] = make_uint2(q.nbr | ((q.code & 1u) << 31), q.code >> 1);
         tc[p] = (int32_t)c;
         codes[p] = q.code;
-        minflag[p] = c < q.nbr ? 1 : 0;
+    }
+};
+
+// The first pass of the pair sort reads the entries and keeps those at the
+// smaller endpoint of their edge (one per edge), keyed by the larger one. The
+// entries are in (centre, rank) order, so the stable sort yields every node
+// pair's edges as one run in rank order.
+struct PairGen {
+    static constexpr bool VEC_KEYS = false;
+    const uint2 *__restrict__ tn;
+    const int32_t *__restrict__ tc;
+    __device__ __forceinline__ bool valid(int64_t p) const {
+        return (uint32_t)tc[p] < (tn[p].x & 0x7fffffffu);
+    }
+    __device__ __forceinline__ uint32_t key(int64_t p) const { return tn[p].x & 0x7fffffffu; }
+    __device__ __forceinline__ PairPayload val(int64_t p) const {
+        const uint2 e = tn[p];
+        PairPayload q;
+        q.pos = (uint32_t)p;
+        q.centre = (uint32_t)tc[p];
+        q.rank = (int32_t)e.y;
+        q.srcmin = (e.x >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
+        return q;
     }
 };
 
@@ -146,40 +168,75 @@ __global__ void k_pos_scatter(const uint32_t *__restrict__ codes, int64_t n2, ui
     }
 }
 
-// The entries at the smaller endpoint of each edge, keyed by the larger one.
-// In T order (centre, then rank); a stable sort by the key then yields every
-// node pair's edges as one run in rank order.
-__global__ void k_pair_compact(const uint2 *__restrict__ tn, const int32_t *__restrict__ tc,
-                               const int32_t *__restrict__ minflag, const int32_t *__restrict__ idx,
-                               int64_t n2, uint32_t *__restrict__ keys,
-                               PairPayload *__restrict__ vals) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        if (minflag[p]) {
-            const uint2 e = tn[p];
-            const int32_t k = idx[p];
-            keys[k] = e.x & 0x7fffffffu;
-            PairPayload q;
-            q.pos = (uint32_t)p;
-            q.centre = (uint32_t)tc[p];
-            q.rank = (int32_t)e.y;
-            q.srcmin = (e.x >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
-            vals[k] = q;
+// Pair list element k (one edge of the node pair (centre, pkey[k]), in rank
+// order): its rank into pl, whether its source is the smaller id, whether it
+// starts a new node pair, and the same-neighbour links of its two entries.
+// Consecutive edges of one node pair are consecutive same-neighbour entries at
+// both of its nodes. Entries whose pair has one edge keep the links of the
+// memset (-1, -1); the others get their whole (prev, next) from their own
+// element. A warp takes 32 consecutive elements and passes the neighbouring
+// elements' keys and entry positions along with shuffles.
+__global__ void k_pair_links(const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
+                             const int32_t *__restrict__ pos_src,
+                             const int32_t *__restrict__ pos_dst, int64_t m, int2 *__restrict__ pl,
+                             int32_t *__restrict__ srcmin, int32_t *__restrict__ head,
+                             int2 *__restrict__ lk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5 << 5; base < m;
+         base += nwarps * 32) {
+        const int64_t k = base + lane;
+        const bool in = k < m;
+        PairPayload q{};
+        uint32_t key = 0xffffffffu;
+        if (in) {
+            q = pp[k];
+            key = pkey[k];
         }
-    }
-}
-
-// Pair list k: the edge's rank, whether its source is the smaller id, and
-// whether k starts a new node pair.
-__global__ void k_pair_flags(const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
-                             int64_t m, int2 *__restrict__ pl, int32_t *__restrict__ srcmin,
-                             int32_t *__restrict__ head) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const PairPayload q = pp[k];
+        // the neighbouring elements: shuffles inside the warp, loads across its edges
+        uint32_t key_p = __shfl_up_sync(0xffffffffu, key, 1);
+        uint32_t cen_p = __shfl_up_sync(0xffffffffu, q.centre, 1);
+        uint32_t key_n = __shfl_down_sync(0xffffffffu, key, 1);
+        uint32_t cen_n = __shfl_down_sync(0xffffffffu, q.centre, 1);
+        PairPayload qp{}, qn{};
+        if (in && lane == 0 && k > 0) {
+            qp = pp[k - 1];
+            key_p = pkey[k - 1];
+            cen_p = qp.centre;
+        }
+        if (in && (lane == 31 || k + 1 == m)) {
+            key_n = 0xffffffffu;
+            if (k + 1 < m) {
+                qn = pp[k + 1];
+                key_n = pkey[k + 1];
+                cen_n = qn.centre;
+            }
+        }
+        const bool same_p = in && k > 0 && key_p == key && cen_p == q.centre;
+        const bool same_n = in && k + 1 < m && key_n == key && cen_n == q.centre;
+        // entry position at the larger endpoint, for elements with a neighbour
+        int32_t big = -1;
+        if (same_p || same_n) big = q.srcmin ? pos_dst[q.rank] : pos_src[q.rank];
+        int32_t pos_p = __shfl_up_sync(0xffffffffu, (int32_t)q.pos, 1);
+        int32_t big_p = __shfl_up_sync(0xffffffffu, big, 1);
+        int32_t pos_n = __shfl_down_sync(0xffffffffu, (int32_t)q.pos, 1);
+        int32_t big_n = __shfl_down_sync(0xffffffffu, big, 1);
+        if (!in) continue;
+        if (lane == 0 && same_p) {
+            pos_p = (int32_t)qp.pos;
+            big_p = qp.srcmin ? pos_dst[qp.rank] : pos_src[qp.rank];
+        }
+        if (lane == 31 && same_n) {
+            pos_n = (int32_t)qn.pos;
+            big_n = qn.srcmin ? pos_dst[qn.rank] : pos_src[qn.rank];
+        }
         pl[k].x = q.rank;
         srcmin[k] = (int32_t)q.srcmin;
-        head[k] = (k == 0 || pkey[k] != pkey[k - 1] || q.centre != pp[k - 1].centre) ? 1 : 0;
+        head[k] = same_p ? 0 : 1;
+        if (same_p || same_n) {
+            lk[q.pos] = make_int2(same_p ? pos_p : -1, same_n ? pos_n : -1);
+            lk[big] = make_int2(same_p ? big_p : -1, same_n ? big_n : -1);
+        }
     }
 }
 
@@ -188,25 +245,6 @@ __global__ void k_pair_cum(const int32_t *__restrict__ cum, int64_t m, int2 *__r
          k += (int64_t)gridDim.x * blockDim.x) {
         pl[k].y = cum[k];
         if (k == m) pl[k].x = INT_MAX;
-    }
-}
-
-// Consecutive edges of one node pair are consecutive same-neighbour entries
-// at both of its nodes: link their entries.
-__global__ void k_links(const PairPayload *__restrict__ pp, const int32_t *__restrict__ head,
-                        const int32_t *__restrict__ pos_src, const int32_t *__restrict__ pos_dst,
-                        int64_t m, int2 *__restrict__ lk) {
-    for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        if (head[k]) continue;
-        const PairPayload q = pp[k], qp = pp[k - 1];
-        const int32_t cur0 = (int32_t)q.pos, prv0 = (int32_t)qp.pos;
-        const int32_t cur1 = q.srcmin ? pos_dst[q.rank] : pos_src[q.rank];  // larger endpoint
-        const int32_t prv1 = qp.srcmin ? pos_dst[qp.rank] : pos_src[qp.rank];
-        lk[cur0].x = prv0;
-        lk[prv0].y = cur0;
-        lk[cur1].x = prv1;
-        lk[prv1].y = cur1;
     }
 }
 
@@ -292,28 +330,28 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
+void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m;
-    int32_t *idx = dev_alloc_n<int32_t>(n2 + 1, s);
-    exclusive_scan_i32(minflag, idx, n2, s);
     uint32_t *k1 = dev_alloc_n<uint32_t>(m, s), *k2 = dev_alloc_n<uint32_t>(m, s);
     PairPayload *v1 = dev_alloc_n<PairPayload>(m, s), *v2 = dev_alloc_n<PairPayload>(m, s);
-    TM_LAUNCH(k_pair_compact, grid_for(n2), 256, 0, s, g.tn, g.tc, minflag, idx, n2, k1, v1);
-    dev_free(idx, s);
-    uint32_t *sk;
-    PairPayload *sv;
-    radix_sort_u32_pair(k1, v1, k2, v2, m, nb, s, &sk, &sv);
+    // the last pass writes the pair not read by it (see radix::sort)
+    const int passes = nb > 8 ? (nb + 7) / 8 : 1;
+    uint32_t *sk = passes & 1 ? k1 : k2;
+    PairPayload *sv = passes & 1 ? v1 : v2;
+    radix::sort<uint32_t, PairPayload>(PairGen{g.tn, g.tc},
+                                       radix::ArrayOut<uint32_t, PairPayload>{sk, sv}, k1, v1, k2,
+                                       v2, n2, m, nb, s);
 
     int32_t *srcmin = dev_alloc_n<int32_t>(m, s);
     int32_t *head = dev_alloc_n<int32_t>(m, s);
     int32_t *run_id = dev_alloc_n<int32_t>(m + 1, s);
     int32_t *cum = dev_alloc_n<int32_t>(m + 1, s);
-    TM_LAUNCH(k_pair_flags, grid_for(m), 256, 0, s, sk, sv, m, g.pl, srcmin, head);
+    TM_LAUNCH(k_pair_links, grid_for(m), 256, 0, s, sk, sv, g.pos_src, g.pos_dst, m, g.pl, srcmin,
+              head, g.lk);
     exclusive_scan_i32(srcmin, cum, m, s);
     TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, s, cum, m, g.pl);
     dev_free(cum, s);
     exclusive_scan_i32(head, run_id, m, s);
-    TM_LAUNCH(k_links, grid_for(m), 256, 0, s, sv, head, g.pos_src, g.pos_dst, m, g.lk);
     int32_t nruns = 0;
     TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     TM_CUDA(cudaStreamSynchronize(s));
@@ -368,12 +406,12 @@ void build_pairs(DevGraph &g, const int32_t *minflag, int nb, cudaStream_t s) {
 // sorts their 2m incident entries by centre (stable: each S_u stays in rank
 // order): the first pass of the second sort generates the entries from the
 // rank-ordered edges, its last pass writes the entry arrays of g, the entry
-// codes and minflag. Then off, cin and the position arrays. Scratch buffers
+// codes. Then off, cin and the position arrays. Scratch buffers
 // (and, through release_inputs, the edge arrays) are released as soon as the
 // kernels after them no longer read them.
 template <typename K, typename Release>
 void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
-                            int keybits, int nbits, int32_t *minflag, Release release_inputs,
+                            int keybits, int nbits, Release release_inputs,
                             cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m, n = g.n;
     K *sk;
@@ -399,7 +437,7 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     using radix::ArrayIn;
     using radix::ArrayOut;
     const EntryGen<K> gen{sk, sv};
-    const EntryStore out{g.tt, g.tn, g.tc, codes, minflag};
+    const EntryStore out{g.tt, g.tn, g.tc, codes};
     const int passes = nbits > 8 ? (nbits + 7) / 8 : 1;
     const int64_t ntiles = (n2 + radix::Cfg<uint32_t, V>::TILE - 1) / radix::Cfg<uint32_t, V>::TILE;
     int32_t *hist = dev_alloc_n<int32_t>(radix::RADIX * ntiles + 1, s);
@@ -547,18 +585,16 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     // 2-4. rank order, then S_u for every centre
     const int keybits = bits_for(span);
     const int nbits = bits_for((uint64_t)(n - 1));
-    int32_t *minflag = dev_alloc_n<int32_t>(2 * m, s);
     if (keybits <= 32)
-        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, minflag, release_inputs, s);
+        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, release_inputs, s);
     else
-        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, minflag, release_inputs, s);
+        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, release_inputs, s);
 
-    // 5-6. pair list, hash, same-neighbour links
+    // 5-6. pair list, same-neighbour links, hash
     {
         PhaseTimer pt(TM_PH_PAIRS, s);
-        build_pairs(g, minflag, bits_for((uint64_t)(n - 1)), s);
+        build_pairs(g, nbits, s);
     }
-    dev_free(minflag, s);
     TM_CUDA(cudaStreamSynchronize(s));
 }
 

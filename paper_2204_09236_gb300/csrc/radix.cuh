@@ -7,8 +7,10 @@
 // and a stable scatter that ranks a tile in shared memory and writes every
 // digit's run with consecutive addresses.
 //
-// In:  key(i) -> K; val(i) -> V; VEC_KEYS and keys (for 128-bit key loads)
-// Out: store(g, K, const V&)
+// In:  valid(i) (whether item i takes part: a first pass may drop items),
+//      key(i) -> K, val(i) -> V; VEC_KEYS and keys (128-bit key loads, only
+//      for inputs whose items are all valid)
+// Out: store(g, K, const V&), g in [0, number of valid items)
 #pragma once
 
 #include <atomic>
@@ -74,6 +76,7 @@ struct ArrayIn {
     static constexpr bool VEC_KEYS = true;
     const K *__restrict__ keys;
     const V *__restrict__ vals;
+    __device__ __forceinline__ bool valid(int64_t) const { return true; }
     __device__ __forceinline__ K key(int64_t i) const { return keys[i]; }
     __device__ __forceinline__ V val(int64_t i) const { return vals[i]; }
 };
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(THREADS)
         }
     } else {
         for (int li = threadIdx.x; li < tile_n; li += THREADS)
-            atomicAdd(&h[warp][digit_of(in.key(tbase + li), shift)], 1);
+            if (in.valid(tbase + li)) atomicAdd(&h[warp][digit_of(in.key(tbase + li), shift)], 1);
     }
     __syncthreads();
     int c = 0;
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(THREADS, 4)
     V *sv = reinterpret_cast<V *>(sk + TILE);               // [TILE]
     __shared__ int digit_off[RADIX];
     __shared__ int gbase[RADIX];
+    __shared__ int tile_valid;  // items of the tile that take part
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t tbase = (int64_t)blockIdx.x * TILE;
@@ -167,18 +171,20 @@ __global__ void __launch_bounds__(THREADS, 4)
     K key[ITEMS];
     V val[ITEMS];
     int rnk[ITEMS];
+    unsigned ok = 0;  // bit r: item r of this lane takes part
     const unsigned lt_mask = (1u << lane) - 1u;
     const int wofs = warp * 32 * ITEMS;
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
         const int li = wofs + r * 32 + lane;
-        key[r] = li < tile_n ? in.key(tbase + li) : K(0);
+        const bool v = li < tile_n && in.valid(tbase + li);
+        ok |= (unsigned)v << r;
+        key[r] = v ? in.key(tbase + li) : K(0);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
-        const int li = wofs + r * 32 + lane;
-        const int d = li < tile_n ? digit_of(key[r], shift) : RADIX;
+        const int d = (ok >> r) & 1u ? digit_of(key[r], shift) : RADIX;
         const unsigned peers = warp_peers9(d);
         const int leader = __ffs(peers) - 1;
         int base = 0;
@@ -187,10 +193,8 @@ __global__ void __launch_bounds__(THREADS, 4)
         rnk[r] = base + __popc(peers & lt_mask);
     }
 #pragma unroll
-    for (int r = 0; r < ITEMS; r++) {
-        const int li = wofs + r * 32 + lane;
-        val[r] = li < tile_n ? in.val(tbase + li) : V{};
-    }
+    for (int r = 0; r < ITEMS; r++)
+        val[r] = (ok >> r) & 1u ? in.val(tbase + wofs + r * 32 + lane) : V{};
     __syncthreads();
     {
         // digit `tid`: exclusive prefix over the warps, then over the digits
@@ -201,16 +205,14 @@ __global__ void __launch_bounds__(THREADS, 4)
             cnt[w * RADIX + tid] = tot;
             tot += c;
         }
-        __shared__ int total;
-        const int ex = block_excl_scan<THREADS>(tot, &total);
+        const int ex = block_excl_scan<THREADS>(tot, &tile_valid);
         digit_off[tid] = ex;
         gbase[tid] = base_off[(int64_t)tid * ntiles + blockIdx.x];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
-        const int li = wofs + r * 32 + lane;
-        if (li < tile_n) {
+        if ((ok >> r) & 1u) {
             const int d = digit_of(key[r], shift);
             const int pos = digit_off[d] + cnt[warp * RADIX + d] + rnk[r];
             sk[pos] = key[r];
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, 4)
         }
     }
     __syncthreads();
-    for (int li = tid; li < tile_n; li += THREADS) {
+    for (int li = tid; li < tile_valid; li += THREADS) {
         const K k = sk[li];
         const int d = digit_of(k, shift);
         out.store((int64_t)gbase[d] + (li - digit_off[d]), k, sv[li]);
@@ -230,8 +232,8 @@ constexpr size_t scatter_smem() {
     return sizeof(int) * WARPS * RADIX + (sizeof(K) + sizeof(V)) * Cfg<K, V>::TILE;
 }
 
-// One pass from `in` to `out` on digit `shift`; hist holds RADIX * ntiles + 1
-// counters.
+// One pass from the n items of `in` (valid or not) to `out` on digit `shift`;
+// hist holds RADIX * ntiles + 1 counters.
 template <typename K, typename V, typename In, typename Out>
 void pass(In in, Out out, int64_t n, int shift, int32_t *hist, cudaStream_t s) {
     constexpr int TILE = Cfg<K, V>::TILE;
@@ -251,21 +253,26 @@ void pass(In in, Out out, int64_t n, int shift, int32_t *hist, cudaStream_t s) {
               shift, hist, ntiles);
 }
 
-// Sorts n items on the low `bits` bits of their keys (at least one pass, so
-// that `out` is always written): the first pass reads `in`, the last writes
-// `out`, the passes between ping-pong through (ka, va) and (kb, vb).
+// Sorts the n valid items of the n_in items of `in` on the low `bits` bits of
+// their keys (at least one pass, so that `out` is always written): the first
+// pass reads `in`, the last writes `out`, the passes between ping-pong through
+// (ka, va) and (kb, vb), which hold n items each. `out` must not be the buffer
+// pair the last pass reads: (kb, vb) after an odd number of passes above one,
+// (ka, va) after an even number.
 template <typename K, typename V, typename In, typename Out>
-void sort(In in, Out out, K *ka, V *va, K *kb, V *vb, int64_t n, int bits, cudaStream_t s) {
-    if (n <= 0) return;
+void sort(In in, Out out, K *ka, V *va, K *kb, V *vb, int64_t n_in, int64_t n, int bits,
+          cudaStream_t s) {
+    if (n_in <= 0) return;
     if ((reinterpret_cast<uintptr_t>(ka) | reinterpret_cast<uintptr_t>(kb)) & 15)
         fail(TM_EINVAL, "radix sort: key buffers must be 16-byte aligned");
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
-    const int64_t ntiles = (n + Cfg<K, V>::TILE - 1) / Cfg<K, V>::TILE;
+    const int64_t nmax = n_in > n ? n_in : n;
+    const int64_t ntiles = (nmax + Cfg<K, V>::TILE - 1) / Cfg<K, V>::TILE;
     int32_t *hist = dev_alloc_n<int32_t>(RADIX * ntiles + 1, s);
     if (passes == 1) {
-        pass<K, V>(in, out, n, 0, hist, s);
+        pass<K, V>(in, out, n_in, 0, hist, s);
     } else {
-        pass<K, V>(in, ArrayOut<K, V>{ka, va}, n, 0, hist, s);
+        pass<K, V>(in, ArrayOut<K, V>{ka, va}, n_in, 0, hist, s);
         K *kc = ka, *kn = kb;
         V *vc = va, *vn = vb;
         for (int p = 1; p + 1 < passes; p++) {

@@ -126,7 +126,7 @@ void radix_sort_impl(K *keys, V *vals, K *keys_tmp, V *vals_tmp, int64_t n, int 
     K *kf = passes & 1 ? keys_tmp : keys;
     V *vf = passes & 1 ? vals_tmp : vals;
     radix::sort<K, V>(radix::ArrayIn<K, V>{keys, vals}, radix::ArrayOut<K, V>{kf, vf}, keys_tmp,
-                      vals_tmp, keys, vals, n, bits, s);
+                      vals_tmp, keys, vals, n, n, bits, s);
     *keys_out = kf;
     *vals_out = vf;
 }
