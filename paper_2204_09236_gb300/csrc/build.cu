@@ -12,6 +12,7 @@
 //   6. links between consecutive same-neighbour entries of a centre
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "radix.cuh"
@@ -83,7 +84,7 @@ __global__ void k_time_keys(const int32_t *__restrict__ src, const int32_t *__re
 // edge of that rank sits at its source (side 0, direction o) or destination
 // (side 1, direction in), keyed by that centre and carrying its timestamp, its
 // neighbour and (rank << 1) | side.
-template <typename TK>
+template <typename TK, typename V>
 struct EntryGen {
     static constexpr bool VEC_KEYS = false;
     const TK *__restrict__ tkey;      // t - t_min in rank order
@@ -93,23 +94,24 @@ struct EntryGen {
         const uint64_t v = sd[i >> 1];
         return (i & 1) ? (uint32_t)v : (uint32_t)(v >> 32);
     }
-    __device__ __forceinline__ EntryPayload val(int64_t i) const {
+    __device__ __forceinline__ V val(int64_t i) const {
         const uint64_t v = sd[i >> 1];
         const uint32_t other = (i & 1) ? (uint32_t)(v >> 32) : (uint32_t)v;
-        return EntryPayload{(int64_t)tkey[i >> 1], other, (uint32_t)i};
+        return V{static_cast<decltype(V::t)>(tkey[i >> 1]), other, (uint32_t)i};
     }
 };
 
 // The last pass of the centre sort writes every entry in its final form: the
 // entry arrays and its code (rank << 1 | side) for the position scatter and
 // the in-prefix.
+template <typename V>
 struct EntryStore {
     int64_t *__restrict__ tt;
     uint2 *__restrict__ tn;
     int32_t *__restrict__ tc;
     uint32_t *__restrict__ codes;
-    __device__ __forceinline__ void store(int64_t p, uint32_t c, const EntryPayload &q) const {
-        tt[p] = q.t;
+    __device__ __forceinline__ void store(int64_t p, uint32_t c, const V &q) const {
+        tt[p] = (int64_t)q.t;
         tn[p] = make_uint2(q.nbr | ((q.code & 1u) << 31), q.code >> 1);
         tc[p] = (int32_t)c;
         codes[p] = q.code;
@@ -130,12 +132,9 @@ struct PairGen {
     __device__ __forceinline__ uint32_t key(int64_t p) const { return tn[p].x & 0x7fffffffu; }
     __device__ __forceinline__ PairPayload val(int64_t p) const {
         const uint2 e = tn[p];
-        PairPayload q;
-        q.pos = (uint32_t)p;
-        q.centre = (uint32_t)tc[p];
-        q.rank = (int32_t)e.y;
-        q.srcmin = (e.x >> 31) ? 0u : 1u;  // o at the smaller endpoint: it is the source
-        return q;
+        // o at the smaller endpoint: it is the source
+        const uint32_t srcmin = (e.x >> 31) ? 0u : 1u;
+        return PairPayload{(uint32_t)p | (srcmin << 31), (uint32_t)tc[p], (int32_t)e.y};
     }
 };
 
@@ -216,25 +215,25 @@ __global__ void k_pair_links(const uint32_t *__restrict__ pkey, const PairPayloa
         const bool same_n = in && k + 1 < m && key_n == key && cen_n == q.centre;
         // entry position at the larger endpoint, for elements with a neighbour
         int32_t big = -1;
-        if (same_p || same_n) big = q.srcmin ? pos_dst[q.rank] : pos_src[q.rank];
-        int32_t pos_p = __shfl_up_sync(0xffffffffu, (int32_t)q.pos, 1);
+        if (same_p || same_n) big = q.srcmin() ? pos_dst[q.rank] : pos_src[q.rank];
+        int32_t pos_p = __shfl_up_sync(0xffffffffu, (int32_t)q.pos(), 1);
         int32_t big_p = __shfl_up_sync(0xffffffffu, big, 1);
-        int32_t pos_n = __shfl_down_sync(0xffffffffu, (int32_t)q.pos, 1);
+        int32_t pos_n = __shfl_down_sync(0xffffffffu, (int32_t)q.pos(), 1);
         int32_t big_n = __shfl_down_sync(0xffffffffu, big, 1);
         if (!in) continue;
         if (lane == 0 && same_p) {
-            pos_p = (int32_t)qp.pos;
-            big_p = qp.srcmin ? pos_dst[qp.rank] : pos_src[qp.rank];
+            pos_p = (int32_t)qp.pos();
+            big_p = qp.srcmin() ? pos_dst[qp.rank] : pos_src[qp.rank];
         }
         if (lane == 31 && same_n) {
-            pos_n = (int32_t)qn.pos;
-            big_n = qn.srcmin ? pos_dst[qn.rank] : pos_src[qn.rank];
+            pos_n = (int32_t)qn.pos();
+            big_n = qn.srcmin() ? pos_dst[qn.rank] : pos_src[qn.rank];
         }
         pl[k].x = q.rank;
-        srcmin[k] = (int32_t)q.srcmin;
+        srcmin[k] = (int32_t)q.srcmin();
         head[k] = same_p ? 0 : 1;
         if (same_p || same_n) {
-            lk[q.pos] = make_int2(same_p ? pos_p : -1, same_n ? pos_n : -1);
+            lk[q.pos()] = make_int2(same_p ? pos_p : -1, same_n ? pos_n : -1);
             lk[big] = make_int2(same_p ? big_p : -1, same_n ? big_n : -1);
         }
     }
@@ -275,7 +274,7 @@ __global__ void k_hash_records(const int32_t *__restrict__ run_begin, int64_t nr
         atomicOr(&bloom[word], (unsigned long long)bits);
         if (e - b == 1) {
             b = -(q.rank + 1);
-            e = (int32_t)q.srcmin;
+            e = (int32_t)q.srcmin();
         }
         region[j] = (hash_pair(key) & mask) >> region_shift;
         rec[j] = HashRecord{key, b, e};
@@ -433,11 +432,12 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     }
     PhaseTimer pt(TM_PH_INCIDENT, s);
     uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);
-    using V = EntryPayload;
+    // a 32-bit time key travels as a 32-bit timestamp
+    using V = std::conditional_t<sizeof(K) == 4, EntryPayload32, EntryPayload>;
     using radix::ArrayIn;
     using radix::ArrayOut;
-    const EntryGen<K> gen{sk, sv};
-    const EntryStore out{g.tt, g.tn, g.tc, codes};
+    const EntryGen<K, V> gen{sk, sv};
+    const EntryStore<V> out{g.tt, g.tn, g.tc, codes};
     const int passes = nbits > 8 ? (nbits + 7) / 8 : 1;
     const int64_t ntiles = (n2 + radix::Cfg<uint32_t, V>::TILE - 1) / radix::Cfg<uint32_t, V>::TILE;
     int32_t *hist = dev_alloc_n<int32_t>(radix::RADIX * ntiles + 1, s);

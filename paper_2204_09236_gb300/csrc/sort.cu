@@ -51,15 +51,20 @@ __global__ void k_scan_sums(int32_t *sums, int64_t n) {
     }
 }
 
+// Shared-memory index of tile element i, padded by one word per 32 so that
+// both the coalesced phase (thread t touches t + 256 r) and the per-thread
+// phase (thread t touches 16 t + k) are free of bank conflicts.
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
 template <typename T, typename F>
 __global__ void k_tile_apply(const T *in, int32_t *out, int64_t n, const int32_t *__restrict__ sums,
                              F f) {
-    __shared__ int32_t tile[SCAN_TILE];
+    __shared__ int32_t tile[SCAN_TILE + SCAN_TILE / 32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
 #pragma unroll
     for (int r = 0; r < SCAN_ITEMS; r++) {
         int64_t i = base + r * SCAN_THREADS + threadIdx.x;
-        tile[r * SCAN_THREADS + threadIdx.x] = i < n ? f(in[i]) : 0;
+        tile[scan_pad(r * SCAN_THREADS + threadIdx.x)] = i < n ? f(in[i]) : 0;
     }
     __syncthreads();
     int loc[SCAN_ITEMS];
@@ -67,17 +72,17 @@ __global__ void k_tile_apply(const T *in, int32_t *out, int64_t n, const int32_t
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
         loc[k] = acc;
-        acc += tile[threadIdx.x * SCAN_ITEMS + k];
+        acc += tile[scan_pad(threadIdx.x * SCAN_ITEMS + k)];
     }
     __shared__ int total;
     int ex = block_excl_scan<SCAN_THREADS>(acc, &total) + sums[blockIdx.x];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; k++) tile[threadIdx.x * SCAN_ITEMS + k] = ex + loc[k];
+    for (int k = 0; k < SCAN_ITEMS; k++) tile[scan_pad(threadIdx.x * SCAN_ITEMS + k)] = ex + loc[k];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < SCAN_ITEMS; r++) {
         int64_t i = base + r * SCAN_THREADS + threadIdx.x;
-        if (i < n) out[i] = tile[r * SCAN_THREADS + threadIdx.x];
+        if (i < n) out[i] = tile[scan_pad(r * SCAN_THREADS + threadIdx.x)];
     }
     if (base + SCAN_TILE >= n && threadIdx.x == 0) {
         // the last tile also writes the grand total

@@ -149,14 +149,22 @@ struct EntryPayload {
     uint32_t nbr;   // the other endpoint
     uint32_t code;  // (rank << 1) | side, side 1 = at the destination (inward)
 };
+// The same with a 32-bit timestamp, for graphs whose timestamp span fits 32
+// bits (12 bytes instead of 16 through every pass of the sort).
+struct EntryPayload32 {
+    uint32_t t;
+    uint32_t nbr;
+    uint32_t code;
+};
 // Payload of an edge while the pair list is sorted: the position of its
-// entry at the smaller endpoint, that endpoint, the edge's rank and whether
-// the smaller endpoint is its source.
+// entry at the smaller endpoint with, in bit 31, whether the smaller endpoint
+// is its source; that endpoint; the edge's rank.
 struct PairPayload {
-    uint32_t pos;
+    uint32_t ps;
     uint32_t centre;
     int32_t rank;
-    uint32_t srcmin;
+    __host__ __device__ uint32_t pos() const { return ps & 0x7fffffffu; }
+    __host__ __device__ uint32_t srcmin() const { return ps >> 31; }
 };
 // One pair-hash insertion: the pair key and its run (or single edge).
 struct HashRecord {
