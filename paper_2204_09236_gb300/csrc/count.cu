@@ -379,32 +379,50 @@ __device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int
 // The join of one edge e_j = u -> w (u its source): the smaller of the two
 // endpoint windows is enumerated, the matches are looked up in the other.
 struct TriEdge {
-    uint32_t u, w;
-    int32_t rank_j;
     int32_t small_lo;     // smaller window: entries [small_lo, small_lo + work)
     int32_t work;
     int32_t rank_lo_big;  // rank of the first entry of the bigger window
-    int32_t small_is_u;   // 1: the smaller window is W_u
-    int32_t pad;
+    uint32_t rj_s;        // rank of e_j; bit 31: the smaller window is W_u
+    uint32_t big;         // the bigger window's centre
+    __device__ __forceinline__ int32_t rank_j() const { return (int32_t)(rj_s & 0x7fffffffu); }
+    __device__ __forceinline__ bool small_is_u() const { return (rj_s >> 31) != 0; }
 };
+
+// The join of edge e_j (rank rank_j, source entry r at centre u, other endpoint
+// w, entry twin at w) given both window starts, when both windows are
+// non-empty.
+__device__ __forceinline__ TriEdge make_tri_edge(const DevGraph &g, int32_t r, uint32_t u,
+                                                 uint32_t w, int32_t rank_j, int32_t lo_u,
+                                                 int32_t twin, int32_t lo_w) {
+    const int32_t wu = r - lo_u, ww = twin - lo_w;
+    const bool su = wu <= ww;
+    TriEdge E;
+    E.small_lo = su ? lo_u : lo_w;
+    E.work = su ? wu : ww;
+    E.rank_lo_big = (int32_t)g.tn[su ? lo_w : lo_u].y;
+    E.rj_s = (uint32_t)rank_j | (su ? 0x80000000u : 0u);
+    E.big = su ? w : u;
+    return E;
+}
 
 // Tri type-II cells: acc[IX(di, dj, dk)]. At the source u, e_j is outward
 // (dj = 0); at the destination w it is inward (dj = 1). A match ranked after
 // the item is centred at the item's centre, one ranked before it at the big
 // window's centre.
-__device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, const TriEdge &E,
+__device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, uint32_t big,
+                                                 int32_t rank_lo_big, uint32_t rj_s,
                                                  const uint2 it, uint64_t key,
                                                  unsigned long long (&acc)[8]) {
     const uint32_t x = node_of(it.x);
-    const uint32_t big = E.small_is_u ? E.w : E.u;
     PairCounts c;
-    if (!pair_counts_hashed(g, key, E.rank_lo_big, E.rank_j, (int32_t)it.y, c)) return;
+    if (!pair_counts_hashed(g, key, rank_lo_big, (int32_t)(rj_s & 0x7fffffffu), (int32_t)it.y, c))
+        return;
     // a big-side edge big -> x is outward at big and inward at x
     const bool big_is_min = big < x;
     const int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
     const int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
     const int di = dir_of(it.x);                                // item w.r.t. its centre
-    if (E.small_is_u) {
+    if (rj_s >> 31) {  // the smaller window is W_u
         // item a in W_u (node x), matches k in W_w.
         // after a: centre u, (e_i = a, e_k = k): Tri[II][d_a][0][dir of k w.r.t. x]
         // before a: centre w, (e_i = k, e_k = a): Tri[II][dir of k w.r.t. w][1][dir of a w.r.t. x]
@@ -439,46 +457,124 @@ __device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, const TriEdg
 
 constexpr int TRI_WARPS = THREADS / 32;
 
-// Walks S_u entries in order; each edge is taken once, at its source entry
-// (direction o). Each edge e_j = (u -> w) is the later centre edge of the
-// type-II triangles at u and at w, whose other centre edges lie in the
-// windows W_u(e_j) and W_w(e_j), so one join of the two windows on the
-// neighbour node counts both. The probes of the 32 edges of a warp are
-// flattened into one list that all lanes share, so a lane never waits for
-// another lane's long window.
-// Tri joins of the edges whose source entries lie in [begin, end),
-// visited 32 entries at a time by warps wid, wid + nwarps, ...; `edges` and
-// `incl` are the calling warp's shared-memory staging (32 slots each).
-// With LO the window starts are read from wlo (k_window_lo) instead of being
-// searched for.
-template <bool LO>
+// The probes of the (up to) 32 joins staged in edges[] by one warp, `incl`
+// the inclusive prefix of their sizes and `total` its last value: lane j
+// takes probes j, j + 32, ... of the flattened list, so a lane never waits
+// for another lane's long window.
+__device__ __forceinline__ void tri_probes(const DevGraph &g, const TriEdge *edges,
+                                           const int32_t *incl, int32_t total,
+                                           unsigned long long (&acc)[8]) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t jb = 0; jb < total; jb += 32) {
+        const int32_t j = jb + lane;
+        if (j >= total) continue;
+        // owner: the first lane whose inclusive prefix exceeds j
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (incl[mid] > j) hi = mid;
+            else lo = mid + 1;
+        }
+        const TriEdge &B = edges[lo];
+        const uint2 it = g.tn[B.small_lo + (j - (incl[lo] - B.work))];
+        const uint32_t x = node_of(it.x);
+        if (x == B.big) continue;  // an edge of the pair (u, w) itself
+        const uint64_t key = pair_key(B.big, x);
+        uint32_t word;
+        const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
+        if ((load_keep(g.bloom + word) & bits) != bits) continue;  // the pair never met
+        tri_probe_hashed(g, B.big, B.rank_lo_big, B.rj_s, it, key, acc);
+    }
+}
+
+// A probe that passed the Bloom filter, waiting for the hash lookup.
+struct TriProbe {
+    uint2 it;
+    uint64_t key;
+    uint32_t big;
+    int32_t rank_lo_big;
+    uint32_t rj_s;
+    uint32_t pad;
+};
+
+// As tri_probes, in two stages: the Bloom test of every probe, then the hash
+// and pair-list lookups of the fifth that pass it, gathered in the warp's
+// queue q (64 slots, *qn of them in use) and run 32 at a time with every lane
+// busy. Probes still queued when the caller's list ends stay for the next
+// call; tri_flush runs the rest.
+__device__ __forceinline__ void tri_run_queue(const DevGraph &g, TriProbe *q, int n,
+                                              unsigned long long (&acc)[8]) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const TriProbe p = q[lane];
+        tri_probe_hashed(g, p.big, p.rank_lo_big, p.rj_s, p.it, p.key, acc);
+    }
+}
+
+__device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEdge *edges,
+                                                  const int32_t *incl, int32_t total,
+                                                  TriProbe *q, int &qn,
+                                                  unsigned long long (&acc)[8]) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t jb = 0; jb < total; jb += 32) {
+        const int32_t j = jb + lane;
+        bool pass = false;
+        TriProbe p;
+        if (j < total) {
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (incl[mid] > j) hi = mid;
+                else lo = mid + 1;
+            }
+            const TriEdge &B = edges[lo];
+            const uint2 it = g.tn[B.small_lo + (j - (incl[lo] - B.work))];
+            const uint32_t x = node_of(it.x);
+            if (x != B.big) {  // not an edge of the pair (u, w) itself
+                const uint64_t key = pair_key(B.big, x);
+                uint32_t word;
+                const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
+                if ((load_keep(g.bloom + word) & bits) == bits) {
+                    pass = true;
+                    p.it = it;
+                    p.key = key;
+                    p.big = B.big;
+                    p.rank_lo_big = B.rank_lo_big;
+                    p.rj_s = B.rj_s;
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (pass) q[qn + __popc(bal & ((1u << lane) - 1u))] = p;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            tri_run_queue(g, q, 32, acc);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = q[32 + lane];
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+}
+
+// Tri joins of the edges whose source entries lie in [begin, end), visited
+// 32 entries at a time by warps wid, wid + nwarps, ...; each edge is taken
+// once, at its source entry (direction o). Each edge e_j = (u -> w) is the
+// later centre edge of the type-II triangles at u and at w, whose other
+// centre edges lie in the windows W_u(e_j) and W_w(e_j), so one join of the
+// two windows on the neighbour node counts both. `edges` and `incl` are the
+// calling warp's shared-memory staging (32 slots each).
 __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int64_t begin,
                                           int64_t end, int64_t wid, int64_t nwarps,
-                                          const int32_t *__restrict__ wlo, TriEdge *edges,
-                                          int32_t *incl, unsigned long long (&acc)[8]) {
+                                          TriEdge *edges, int32_t *incl,
+                                          unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = begin + wid * 32; base < end; base += nwarps * 32) {
         const int64_t r = base + lane;
         TriEdge E;
         E.work = 0;
-        if (LO && r < end) {
-            const uint2 en = g.tn[r];
-            const int32_t lo_u = wlo[r];
-            if (dir_of(en.x) == 0 && lo_u < r) {
-                const int32_t twin = g.pos_dst[en.y];
-                const int32_t lo_w = wlo[twin];
-                if (lo_w < twin) {
-                    const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
-                    E.u = (uint32_t)g.tc[r];
-                    E.w = node_of(en.x);
-                    E.rank_j = (int32_t)en.y;
-                    E.small_is_u = wu <= ww;
-                    E.small_lo = E.small_is_u ? lo_u : lo_w;
-                    E.work = E.small_is_u ? wu : ww;
-                    E.rank_lo_big = (int32_t)g.tn[E.small_is_u ? lo_w : lo_u].y;
-                }
-            }
-        } else if (!LO && r < end) {
+        if (r < end) {
             const uint2 en = g.tn[r];
             if (dir_of(en.x) == 0) {
                 const int64_t et = g.tt[r];
@@ -491,14 +587,7 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
                     if (twin > wb && et - g.tt[twin - 1] <= delta) {
                         const int32_t lo_u = gallop_lo(g.tt, sb, (int32_t)r, et - delta);
                         const int32_t lo_w = gallop_lo(g.tt, wb, twin, et - delta);
-                        const int32_t wu = (int32_t)r - lo_u, ww = twin - lo_w;
-                        E.u = u;
-                        E.w = w;
-                        E.rank_j = (int32_t)en.y;
-                        E.small_is_u = wu <= ww;
-                        E.small_lo = E.small_is_u ? lo_u : lo_w;
-                        E.work = E.small_is_u ? wu : ww;
-                        E.rank_lo_big = (int32_t)g.tn[E.small_is_u ? lo_w : lo_u].y;
+                        E = make_tri_edge(g, (int32_t)r, u, w, (int32_t)en.y, lo_u, twin, lo_w);
                     }
                 }
             }
@@ -509,51 +598,129 @@ __device__ __forceinline__ void tri_range(const DevGraph &g, int64_t delta, int6
         edges[lane] = E;
         incl[lane] = inc;
         __syncwarp();
-        for (int32_t jb = 0; jb < total; jb += 32) {
-            const int32_t j = jb + lane;
-            if (j >= total) continue;
-            // owner: the first lane whose inclusive prefix exceeds j
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (incl[mid] > j) hi = mid;
-                else lo = mid + 1;
-            }
-            const TriEdge &B = edges[lo];
-            const uint2 it = g.tn[B.small_lo + (j - (incl[lo] - B.work))];
-            const uint32_t x = node_of(it.x);
-            const uint32_t big = B.small_is_u ? B.w : B.u;
-            if (x == big) continue;  // an edge of the pair (u, w) itself
-            const uint64_t key = pair_key(big, x);
-            uint32_t word;
-            const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
-            if ((load_keep(g.bloom + word) & bits) != bits) continue;  // the pair never met
-            tri_probe_hashed(g, B, it, key, acc);
-        }
+        tri_probes(g, edges, incl, total, acc);
         __syncwarp();
     }
 }
 
-// Walks S_u entries in order; each edge is taken once, at its source entry
-// (direction o). Each edge e_j = (u -> w) is the later centre edge of the
-// type-II triangles at u and at w, whose other centre edges lie in the
-// windows W_u(e_j) and W_w(e_j), so one join of the two windows on the
-// neighbour node counts both. The probes of the 32 edges of a warp are
-// flattened into one list that all lanes share, so a lane never waits for
-// another lane's long window.
-template <bool LO>
+// Whole-graph Tri (type II) over the entries [begin, end) without scratch:
+// the window starts are searched for here.
 __global__ void __launch_bounds__(THREADS)
     k_tri(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-          const int32_t *__restrict__ wlo, unsigned long long *__restrict__ cells) {
+          unsigned long long *__restrict__ cells) {
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
     unsigned long long acc[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
     const int warp = threadIdx.x >> 5;
-    tri_range<LO>(g, delta, begin, end, blockIdx.x * (int64_t)TRI_WARPS + warp,
-                  (int64_t)gridDim.x * TRI_WARPS, wlo, edges[warp], incl[warp], acc);
+    tri_range(g, delta, begin, end, blockIdx.x * (int64_t)TRI_WARPS + warp,
+              (int64_t)gridDim.x * TRI_WARPS, edges[warp], incl[warp], acc);
     // type II lives at Tri cells 8..15 (T = 1)
+    block_flush<8, 0>(acc, 32 + 8, cells);
+}
+
+// Whole-graph Tri in two steps, with the window starts wlo of k_window_lo.
+// k_tri_jobs: one thread per entry; every edge (at its source entry) whose
+// two windows are both non-empty becomes one join, appended to `jobs`. The
+// order of the jobs is immaterial: each adds its counts. Only a quarter of the
+// edges have such a join on the large workloads, so the joining warps below
+// get full lists instead of sparse ones, and the chain of dependent reads that
+// finds a join is paid here, in a kernel that does nothing else. A warp
+// gathers its jobs in shared memory and reserves space in `jobs` 32 at a time,
+// so the shared counter takes one atomic per 32 jobs.
+__global__ void __launch_bounds__(THREADS)
+    k_tri_jobs(const DevGraph g, const int32_t *__restrict__ wlo, TriEdge *__restrict__ jobs,
+               int32_t *__restrict__ njobs) {
+    constexpr int U = 4;  // groups of 32 entries per warp and step: U chains of reads in flight
+    __shared__ TriEdge buf[TRI_WARPS][32 * (U + 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TriEdge *wb = buf[warp];
+    int cnt = 0;  // jobs held in wb (warp-uniform, < 32 between steps)
+    const int64_t n2 = 2 * g.m;
+    const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 * U);
+         base < n2; base += nwarps * 32 * U) {
+        uint2 en[U];
+        int32_t lo_u[U], twin[U], lo_w[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t r = base + k * 32 + lane;
+            en[k] = make_uint2(0x80000000u, 0);  // inward: no join
+            lo_u[k] = 0;
+            if (r < n2) {
+                en[k] = g.tn[r];
+                lo_u[k] = wlo[r];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t r = base + k * 32 + lane;
+            twin[k] = -1;
+            if (dir_of(en[k].x) == 0 && lo_u[k] < r) twin[k] = g.pos_dst[en[k].y];
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) lo_w[k] = twin[k] >= 0 ? wlo[twin[k]] : 0;
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t r = base + k * 32 + lane;
+            const bool has = twin[k] >= 0 && lo_w[k] < twin[k];
+            TriEdge E;
+            if (has)
+                E = make_tri_edge(g, (int32_t)r, (uint32_t)g.tc[r], node_of(en[k].x),
+                                  (int32_t)en[k].y, lo_u[k], twin[k], lo_w[k]);
+            const unsigned bal = __ballot_sync(0xffffffffu, has);
+            if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        while (cnt >= 32) {
+            int32_t first = 0;
+            if (lane == 0) first = atomicAdd(njobs, 32);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            jobs[first + lane] = wb[cnt - 32 + lane];
+            cnt -= 32;
+            __syncwarp();
+        }
+    }
+    if (cnt > 0) {
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(njobs, cnt);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (lane < cnt) jobs[first + lane] = wb[lane];
+    }
+}
+
+// k_tri_join: each warp takes 32 consecutive jobs and runs their probes as
+// one flattened list, the hash lookups through the warp's queue.
+__global__ void __launch_bounds__(THREADS)
+    k_tri_join(const DevGraph g, const TriEdge *__restrict__ jobs,
+               const int32_t *__restrict__ njobs_ptr, unsigned long long *__restrict__ cells) {
+    __shared__ TriEdge edges[TRI_WARPS][32];
+    __shared__ int32_t incl[TRI_WARPS][32];
+    __shared__ TriProbe queue[TRI_WARPS][64];
+    unsigned long long acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t njobs = *njobs_ptr;
+    const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
+    int qn = 0;
+    for (int64_t base = (blockIdx.x * (int64_t)TRI_WARPS + warp) * 32; base < njobs;
+         base += nwarps * 32) {
+        const int64_t j = base + lane;
+        TriEdge E;
+        E.work = 0;
+        if (j < njobs) E = jobs[j];
+        const int32_t inc = warp_incl_scan_i32(E.work);
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        edges[warp][lane] = E;
+        incl[warp][lane] = inc;
+        __syncwarp();
+        tri_probes_queued(g, edges[warp], incl[warp], total, queue[warp], qn, acc);
+        __syncwarp();
+    }
+    tri_run_queue(g, queue[warp], qn, acc);
     block_flush<8, 0>(acc, 32 + 8, cells);
 }
 
@@ -649,8 +816,7 @@ __global__ void __launch_bounds__(THREADS)
             unsigned long long acc[8];
 #pragma unroll
             for (int c = 0; c < 8; c++) acc[c] = 0;
-            tri_range<false>(g, delta, it.begin, it.end, warp, TRI_WARPS, nullptr, edges[warp],
-                             incl[warp], acc);
+            tri_range(g, delta, it.begin, it.end, warp, TRI_WARPS, edges[warp], incl[warp], acc);
             block_flush<8, 0>(acc, 32 + 8, cells);
         }
     }
@@ -727,9 +893,17 @@ void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool t
     }
     if (tri) {
         PhaseTimer pt(TM_PH_TRI, s);
-        TM_LAUNCH(k_tri<true>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo,
-                  dev_cells);
+        TriEdge *jobs = dev_alloc_n<TriEdge>(g.m, s);  // at most one join per edge
+        int32_t *njobs = dev_alloc_n<int32_t>(1, s);
+        TM_CUDA(cudaMemsetAsync(njobs, 0, sizeof(int32_t), s));
+        TM_LAUNCH(k_tri_jobs, (unsigned)blocks, THREADS, 0, s, g, wlo, jobs, njobs);
+        int per_sm = 0;
+        TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_join, THREADS, 0));
+        TM_LAUNCH(k_tri_join, (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1)), THREADS, 0, s, g,
+                  jobs, njobs, dev_cells);
         if (fill) TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
+        dev_free(jobs, s);
+        dev_free(njobs, s);
     }
     dev_free(wlo, s);
 }
@@ -743,8 +917,7 @@ void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *
     if (blocks > cap) blocks = cap;
     TM_LAUNCH(k_star_pair<false>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n,
               nullptr, dev_cells);
-    TM_LAUNCH(k_tri<false>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, nullptr,
-              dev_cells);
+    TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
 }
 
