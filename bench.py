@@ -40,9 +40,10 @@ UNIT = "edges/s"
 ALGO_BYTES = {"star_pair": 32, "tri": 48, "time_sort": 16, "incident": 48, "pairs": 32,
               "validate": 16}
 
-# DRAM bytes (read + write) of one k_tri launch on the full workload, from one
-# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# (profiles/k_tri_k_star_pair_dram_large_60M.md); None until captured for the current kernel
+# DRAM bytes (read + write) of the Tri phase (k_tri_jobs + k_tri_join) on the
+# full workload, from one ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum (profiles/count_kernels_dram_large_60M.md); None until
+# captured for the current kernels
 TRI_TRAFFIC = {}
 
 WORKLOADS = {
@@ -452,7 +453,8 @@ def main():
         return ALGO_BYTES[phase] * m / (ph[phase] / 1e3) / 1e9 if ph.get(phase) else None
 
     achieved = gbs("tri")
-    roofline = {"bound": "hbm", "kernel": "k_tri", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "tri phase: k_tri_jobs + k_tri_join",
+                "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": TRI_TRAFFIC.get(args.workload) if args.scale == 1.0 else None,
                 "algo_bytes_per_edge": ALGO_BYTES["tri"], "kernel_ms": ph["tri"],

@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(THREADS)
 
 // k_tri_join: each warp takes 32 consecutive jobs and runs their probes as
 // one flattened list, the hash lookups through the warp's queue.
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 5)
     k_tri_join(const DevGraph g, const TriEdge *__restrict__ jobs,
                const int32_t *__restrict__ njobs_ptr, unsigned long long *__restrict__ cells) {
     __shared__ TriEdge edges[TRI_WARPS][32];
