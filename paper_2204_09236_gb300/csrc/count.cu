@@ -161,7 +161,8 @@ __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta
     // the same-neighbour links are followed only when they land inside.
     const bool wnd_back =
         LO ? lr.x >= lo_r : lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
-    const bool wnd_fwd = lr.y >= 0 && r + 1 < seg_end && tt[r + 1] - tr <= delta;
+    // the next same-neighbour entry lies in F(r) exactly when it is within delta
+    const bool wnd_fwd = lr.y >= 0 && tt[lr.y] - tr <= delta;
     if (!wnd_back && !wnd_fwd) return;
     const int64_t cin_end = g.cin[seg_end];
     const int64_t cin_r = g.cin[r];
@@ -228,8 +229,8 @@ __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta
         }
     }
     if (wnd_fwd) {
-        const int32_t hi = gallop_hi(tt, r, seg_end, tr, delta);
-        if (lr.y <= hi) {
+        const int32_t hi = gallop_hi(tt, lr.y, seg_end, tr, delta);  // hi >= lr.y
+        {
             // same-neighbour entries inside F(r): pairs leaving after hi(r)
             uint64_t f0 = 0, f1 = 0;
             int32_t b = lr.y, cur = r;
