@@ -253,8 +253,108 @@ __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta
     }
 }
 
+// The contributions of a back-active entry r (its previous same-neighbour
+// entry p = lk[r].x lies in W(r), lo(r) = lo_r) with the window starts known:
+// r's own W(r) terms, and the F(p) term of p. p's next same-neighbour entry is
+// r, so F(p) holds a same-neighbour entry exactly when r is back-active with
+// p: the F terms of all entries are produced here, by the entries that
+// follow them, and an entry whose predecessor is outside its window does
+// nothing at all.
+__device__ __forceinline__ void star_pair_back_active(const DevGraph &g, int64_t delta, int32_t r,
+                                                      int2 lr, int32_t lo,
+                                                      unsigned long long *sacc) {
+    const int64_t *__restrict__ tt = g.tt;
+    const int32_t u = g.tc[r];
+    const int32_t seg_end = g.off[u + 1];
+    const int64_t tr = tt[r];
+    const int D3 = dir_of(g.tn[r].x);
+    const int64_t cin_end = g.cin[seg_end];
+    const int64_t cin_r = g.cin[r];
+    {
+        // W(r): as in star_pair_entry
+        uint64_t n0 = 0, n1 = 0, c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+        uint64_t X00 = 0, X01 = 0, X10 = 0, X11 = 0, Y00 = 0, Y01 = 0, Y10 = 0, Y11 = 0;
+        int32_t a = lr.x, cur = r;
+        while (a >= lo && a < cur) {  // links strictly decrease: the walk always ends
+            const int da = dir_of(g.tn[a].x);
+            const int64_t cin_a = g.cin[a];
+            const uint64_t between_in = (uint64_t)(cin_r - (cin_a + da));
+            const uint64_t between_o = (uint64_t)(r - a - 1) - between_in;
+            const uint64_t co_a = (uint64_t)(a - cin_a), ci_a = (uint64_t)cin_a;
+            if (da) {
+                c10 += n0;
+                c11 += n1;
+                n1 += 1;
+                X10 += between_o;
+                X11 += between_in;
+                Y10 += co_a;
+                Y11 += ci_a;
+            } else {
+                c00 += n0;
+                c01 += n1;
+                n0 += 1;
+                X00 += between_o;
+                X01 += between_in;
+                Y00 += co_a;
+                Y01 += ci_a;
+            }
+            cur = a;
+            a = g.lk[a].x;
+        }
+        const uint64_t n[2] = {n0, n1};
+        const uint64_t c2s[2][2] = {{c00, c01}, {c10, c11}};
+        const uint64_t X[2][2] = {{X00, X01}, {X10, X11}};
+        const uint64_t Yp[2][2] = {{Y00, Y01}, {Y10, Y11}};
+        const int64_t cin_lo = g.cin[lo];
+        const int64_t co_lo = (int64_t)lo - cin_lo;
+#pragma unroll
+        for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+            for (int d2 = 0; d2 < 2; d2++) {
+                const uint64_t sp = c2s[d1][d2];
+                add_cell(sacc, IX(d1, d2, D3), sp);                                 // Pair
+                add_cell(sacc, 16 + IX(d1, d2, D3), X[d1][d2] - sp);                // Star-II
+                const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;     // C_d1(lo)
+                add_cell(sacc, 8 + IX(d1, d2, D3), Yp[d2][d1] - n[d2] * base - sp);  // Star-I
+                add_cell(sacc, 24 + IX(d1, d2, D3), 0 - sp);                        // Star-III
+            }
+        const int64_t after_in = cin_end - (cin_r + D3);
+        const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
+#pragma unroll
+        for (int d1 = 0; d1 < 2; d1++) {
+            add_cell(sacc, 24 + IX(d1, D3, 0), n[d1] * (uint64_t)after_o);
+            add_cell(sacc, 24 + IX(d1, D3, 1), n[d1] * (uint64_t)after_in);
+        }
+    }
+    {
+        // F(p) of the predecessor p: its same-neighbour entries from r on
+        const int32_t p = lr.x;
+        const int64_t tp = tt[p];
+        const int Dp = dir_of(g.tn[p].x);
+        const int32_t hi = gallop_hi(tt, r, seg_end, tp, delta);  // t_r - t_p <= delta
+        uint64_t f0 = 0, f1 = 0;
+        int32_t b = r, cur = p;
+        while (b > cur && b <= hi) {  // links strictly increase: the walk always ends
+            if (dir_of(g.tn[b].x)) f1 += 1;
+            else f0 += 1;
+            cur = b;
+            b = g.lk[b].y;
+        }
+        const uint64_t f[2] = {f0, f1};
+        const int64_t cin_h1 = (int64_t)g.cin[hi] + dir_of(g.tn[hi].x);  // C_in(hi+1)
+        const int64_t after_in = cin_end - cin_h1;
+        const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
+#pragma unroll
+        for (int d2 = 0; d2 < 2; d2++) {
+            add_cell(sacc, 24 + IX(Dp, d2, 0), 0 - f[d2] * (uint64_t)after_o);
+            add_cell(sacc, 24 + IX(Dp, d2, 1), 0 - f[d2] * (uint64_t)after_in);
+        }
+    }
+}
+
 // Star/Pair contributions of the entries [begin, end), visited by threads
-// tid, tid + nthreads, ...; with LO the window starts are read from wlo.
+// tid, tid + nthreads, ...; with LO the window starts are read from wlo, and
+// only the back-active entries (lk.x >= lo(r), a few percent) do any work.
 template <bool LO>
 __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta, int64_t begin,
                                                 int64_t end, int64_t tid, int64_t nthreads,
@@ -262,13 +362,18 @@ __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta
                                                 unsigned long long *sacc) {
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
-        const int64_t tr = g.tt[r];
-        const uint32_t nbr = g.tn[r].x;
-        const int32_t u = g.tc[r];
-        const int2 lr = g.lk[r];
-        const int32_t lo_r = LO ? wlo[r] : 0;
-        if (dir_of(nbr)) star_pair_entry<1, LO>(g, delta, r, tr, u, lr, lo_r, sacc);
-        else star_pair_entry<0, LO>(g, delta, r, tr, u, lr, lo_r, sacc);
+        if constexpr (LO) {
+            const int2 lr = g.lk[r];
+            const int32_t lo_r = wlo[r];
+            if (lr.x >= lo_r) star_pair_back_active(g, delta, r, lr, lo_r, sacc);
+        } else {
+            const int64_t tr = g.tt[r];
+            const uint32_t nbr = g.tn[r].x;
+            const int32_t u = g.tc[r];
+            const int2 lr = g.lk[r];
+            if (dir_of(nbr)) star_pair_entry<1, false>(g, delta, r, tr, u, lr, 0, sacc);
+            else star_pair_entry<0, false>(g, delta, r, tr, u, lr, 0, sacc);
+        }
     }
 }
 
@@ -287,6 +392,72 @@ __global__ void __launch_bounds__(THREADS)
         if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
         wlo[r] = lo;
     }
+}
+
+// The Star/Pair sweep in two steps, with the window starts of k_window_lo.
+// k_star_active: the back-active entries (lk.x >= lo(r); a few percent, and
+// the only ones with any contribution) appended to `act`, each warp gathering
+// them in shared memory and reserving space 32 at a time. The order of the
+// list is immaterial: every entry adds its counts.
+__global__ void __launch_bounds__(THREADS)
+    k_star_active(const DevGraph g, const int32_t *__restrict__ wlo, int32_t *__restrict__ act,
+                  int32_t *__restrict__ nact) {
+    constexpr int U = 4;  // groups of 32 entries per warp and step
+    __shared__ int32_t buf[THREADS / 32][32 * (U + 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *wb = buf[warp];
+    int cnt = 0;  // entries held in wb (warp-uniform, < 32 between steps)
+    const int64_t n2 = 2 * g.m;
+    const int64_t nwarps = (int64_t)gridDim.x * (THREADS / 32);
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 * U);
+         base < n2; base += nwarps * 32 * U) {
+        bool a[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t r = base + k * 32 + lane;
+            a[k] = r < n2 && g.lk[r].x >= wlo[r];
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const unsigned bal = __ballot_sync(0xffffffffu, a[k]);
+            if (a[k]) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(base + k * 32 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        while (cnt >= 32) {
+            int32_t first = 0;
+            if (lane == 0) first = atomicAdd(nact, 32);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            act[first + lane] = wb[cnt - 32 + lane];
+            cnt -= 32;
+            __syncwarp();
+        }
+    }
+    if (cnt > 0) {
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(nact, cnt);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (lane < cnt) act[first + lane] = wb[lane];
+    }
+}
+
+// k_star_pair_list: the contributions of the listed entries, 32 to a warp
+// with every lane busy.
+__global__ void __launch_bounds__(THREADS, 5)
+    k_star_pair_list(const DevGraph g, int64_t delta, const int32_t *__restrict__ wlo,
+                     const int32_t *__restrict__ act, const int32_t *__restrict__ nact_ptr,
+                     unsigned long long *__restrict__ cells) {
+    __shared__ unsigned long long sacc[32];
+    if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
+    __syncthreads();
+    const int32_t nact = *nact_ptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nact;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = act[i];
+        star_pair_back_active(g, delta, r, g.lk[r], wlo[r], sacc);
+    }
+    __syncthreads();
+    flush_star_pair(sacc, cells);
 }
 
 template <bool LO>
@@ -888,9 +1059,18 @@ void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool t
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
         TM_LAUNCH(k_window_lo, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo);
-        if (star_pair)
-            TM_LAUNCH(k_star_pair<true>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n,
-                      wlo, dev_cells);
+        if (star_pair) {
+            int32_t *act = dev_alloc_n<int32_t>(n + 1, s);  // the list, then its length
+            int32_t *nact = act + n;
+            TM_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
+            TM_LAUNCH(k_star_active, (unsigned)blocks, THREADS, 0, s, g, wlo, act, nact);
+            int per_sm = 0;
+            TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list,
+                                                                  THREADS, 0));
+            TM_LAUNCH(k_star_pair_list, (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1)), THREADS,
+                      0, s, g, delta, wlo, act, nact, dev_cells);
+            dev_free(act, s);
+        }
     }
     if (tri) {
         PhaseTimer pt(TM_PH_TRI, s);
