@@ -380,51 +380,38 @@ __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta
 // lo(r) for every entry r in [begin, end): the first entry of W(r), r itself
 // when the window is empty. Consecutive entries share their centre and most of
 // their window, so the backward searches of a warp read the same lines.
+// With `act`, the back-active entries (lk.x >= lo(r): a few percent, and the
+// only ones with Star/Pair contributions) are listed there as well, each warp
+// gathering them in shared memory and reserving space 32 at a time. The
+// order of the list is immaterial: every entry adds its counts.
 __global__ void __launch_bounds__(THREADS)
     k_window_lo(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-                int32_t *__restrict__ wlo) {
-    for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = (int32_t)i;
-        const int64_t tr = g.tt[r];
-        const int32_t sb = g.off[g.tc[r]];
-        int32_t lo = r;
-        if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
-        wlo[r] = lo;
-    }
-}
-
-// The Star/Pair sweep in two steps, with the window starts of k_window_lo.
-// k_star_active: the back-active entries (lk.x >= lo(r); a few percent, and
-// the only ones with any contribution) appended to `act`, each warp gathering
-// them in shared memory and reserving space 32 at a time. The order of the
-// list is immaterial: every entry adds its counts.
-__global__ void __launch_bounds__(THREADS)
-    k_star_active(const DevGraph g, const int32_t *__restrict__ wlo, int32_t *__restrict__ act,
-                  int32_t *__restrict__ nact) {
-    constexpr int U = 4;  // groups of 32 entries per warp and step
-    __shared__ int32_t buf[THREADS / 32][32 * (U + 1)];
+                int32_t *__restrict__ wlo, int32_t *__restrict__ act,
+                int32_t *__restrict__ nact) {
+    __shared__ int32_t buf[THREADS / 32][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *wb = buf[warp];
     int cnt = 0;  // entries held in wb (warp-uniform, < 32 between steps)
-    const int64_t n2 = 2 * g.m;
-    const int64_t nwarps = (int64_t)gridDim.x * (THREADS / 32);
-    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 * U);
-         base < n2; base += nwarps * 32 * U) {
-        bool a[U];
-#pragma unroll
-        for (int k = 0; k < U; k++) {
-            const int64_t r = base + k * 32 + lane;
-            a[k] = r < n2 && g.lk[r].x >= wlo[r];
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < end;
+         base += nthreads) {
+        const int64_t i = base + lane;
+        bool active = false;
+        if (i < end) {
+            const int32_t r = (int32_t)i;
+            const int64_t tr = g.tt[r];
+            const int32_t sb = g.off[g.tc[r]];
+            int32_t lo = r;
+            if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
+            wlo[r] = lo;
+            active = act != nullptr && lo < r && g.lk[r].x >= lo;
         }
-#pragma unroll
-        for (int k = 0; k < U; k++) {
-            const unsigned bal = __ballot_sync(0xffffffffu, a[k]);
-            if (a[k]) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(base + k * 32 + lane);
-            cnt += __popc(bal);
-        }
+        if (act == nullptr) continue;
+        const unsigned bal = __ballot_sync(0xffffffffu, active);
+        if (active) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+        cnt += __popc(bal);
         __syncwarp();
-        while (cnt >= 32) {
+        if (cnt >= 32) {
             int32_t first = 0;
             if (lane == 0) first = atomicAdd(nact, 32);
             first = __shfl_sync(0xffffffffu, first, 0);
@@ -433,7 +420,7 @@ __global__ void __launch_bounds__(THREADS)
             __syncwarp();
         }
     }
-    if (cnt > 0) {
+    if (act != nullptr && cnt > 0) {
         int32_t first = 0;
         if (lane == 0) first = atomicAdd(nact, cnt);
         first = __shfl_sync(0xffffffffu, first, 0);
@@ -441,8 +428,8 @@ __global__ void __launch_bounds__(THREADS)
     }
 }
 
-// k_star_pair_list: the contributions of the listed entries, 32 to a warp
-// with every lane busy.
+// The Star/Pair sweep of the back-active entries that k_window_lo listed, 32
+// to a warp with every lane busy.
 __global__ void __launch_bounds__(THREADS, 5)
     k_star_pair_list(const DevGraph g, int64_t delta, const int32_t *__restrict__ wlo,
                      const int32_t *__restrict__ act, const int32_t *__restrict__ nact_ptr,
@@ -671,10 +658,14 @@ struct TriProbe {
 
 // As tri_probes, in two stages: the Bloom test of every probe, then the hash
 // and pair-list lookups of the fifth that pass it, gathered in the warp's
-// queue q (64 slots, *qn of them in use) and run 32 at a time with every lane
-// busy. Probes still queued when the caller's list ends stay for the next
-// call; tri_flush runs the rest.
-__device__ __forceinline__ void tri_run_queue(const DevGraph &g, TriProbe *q, int n,
+// queue q (TRI_QUEUE slots, qn of them in use) and run 32 at a time with
+// every lane busy. Each lane tests two probes per step, so that their
+// dependent reads (item, then Bloom word) are in flight together. Probes still
+// queued when the caller's list ends stay for the next call; the caller runs
+// the rest at its end.
+constexpr int TRI_QUEUE = 96;
+
+__device__ __forceinline__ void tri_run_queue(const DevGraph &g, const TriProbe *q, int n,
                                               unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
     if (lane < n) {
@@ -688,42 +679,59 @@ __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEd
                                                   TriProbe *q, int &qn,
                                                   unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
-    for (int32_t jb = 0; jb < total; jb += 32) {
-        const int32_t j = jb + lane;
-        bool pass = false;
-        TriProbe p;
-        if (j < total) {
+    for (int32_t jb = 0; jb < total; jb += 64) {
+        int32_t j[2], own[2];
+        bool ok[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            j[k] = jb + 32 * k + lane;
+            ok[k] = j[k] < total;
+            // owner: the first lane whose inclusive prefix exceeds j
             int lo = 0, hi = 31;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (incl[mid] > j) hi = mid;
+                if (incl[mid] > j[k]) hi = mid;
                 else lo = mid + 1;
             }
-            const TriEdge &B = edges[lo];
-            const uint2 it = g.tn[B.small_lo + (j - (incl[lo] - B.work))];
-            const uint32_t x = node_of(it.x);
-            if (x != B.big) {  // not an edge of the pair (u, w) itself
-                const uint64_t key = pair_key(B.big, x);
-                uint32_t word;
-                const uint64_t bits = bloom_bits(key, g.bloom_mask, &word);
-                if ((load_keep(g.bloom + word) & bits) == bits) {
-                    pass = true;
-                    p.it = it;
-                    p.key = key;
-                    p.big = B.big;
-                    p.rank_lo_big = B.rank_lo_big;
-                    p.rj_s = B.rj_s;
-                }
-            }
+            own[k] = lo;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (pass) q[qn + __popc(bal & ((1u << lane) - 1u))] = p;
-        qn += __popc(bal);
+        uint2 it[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const TriEdge &B = edges[own[k]];
+            it[k] = ok[k] ? g.tn[B.small_lo + (j[k] - (incl[own[k]] - B.work))] : make_uint2(0, 0);
+        }
+        uint64_t key[2], bits[2], bw[2];
+        bool cand[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const uint32_t big = edges[own[k]].big;
+            const uint32_t x = node_of(it[k].x);
+            cand[k] = ok[k] && x != big;  // not an edge of the pair (u, w) itself
+            key[k] = pair_key(big, x);
+            uint32_t word;
+            bits[k] = bloom_bits(key[k], g.bloom_mask, &word);
+            bw[k] = cand[k] ? load_keep(g.bloom + word) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const bool pass = cand[k] && (bw[k] & bits[k]) == bits[k];
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const TriEdge &B = edges[own[k]];
+                TriProbe p;
+                p.it = it[k];
+                p.key = key[k];
+                p.big = B.big;
+                p.rank_lo_big = B.rank_lo_big;
+                p.rj_s = B.rj_s;
+                q[qn + __popc(bal & ((1u << lane) - 1u))] = p;
+            }
+            qn += __popc(bal);
+        }
         __syncwarp();
-        if (qn >= 32) {
-            tri_run_queue(g, q, 32, acc);
-            __syncwarp();
-            if (lane < qn - 32) q[lane] = q[32 + lane];
+        while (qn >= 32) {
+            tri_run_queue(g, q + qn - 32, 32, acc);  // the newest 32: nothing to move
             qn -= 32;
             __syncwarp();
         }
@@ -870,7 +878,7 @@ __global__ void __launch_bounds__(THREADS, 5)
                const int32_t *__restrict__ njobs_ptr, unsigned long long *__restrict__ cells) {
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
-    __shared__ TriProbe queue[TRI_WARPS][64];
+    __shared__ TriProbe queue[TRI_WARPS][TRI_QUEUE];
     unsigned long long acc[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
@@ -1058,12 +1066,15 @@ void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool t
     int32_t *wlo = dev_alloc_n<int32_t>(n, s);
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_window_lo, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo);
+        int32_t *act = nullptr, *nact = nullptr;
         if (star_pair) {
-            int32_t *act = dev_alloc_n<int32_t>(n + 1, s);  // the list, then its length
-            int32_t *nact = act + n;
+            act = dev_alloc_n<int32_t>(n + 1, s);  // the list, then its length
+            nact = act + n;
             TM_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
-            TM_LAUNCH(k_star_active, (unsigned)blocks, THREADS, 0, s, g, wlo, act, nact);
+        }
+        TM_LAUNCH(k_window_lo, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo, act,
+                  nact);
+        if (star_pair) {
             int per_sm = 0;
             TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list,
                                                                   THREADS, 0));
