@@ -152,19 +152,46 @@ __global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64
 // pos_src / pos_dst[rank] = position of the edge's entry at its source /
 // destination, for the ranks in [rlo, rhi) only. The build runs this once per
 // rank range whose part of the two arrays fits in L2, so the random 4-byte
-// stores merge in L2 instead of each costing a DRAM read-modify-write.
+// stores merge in L2 instead of each costing a DRAM read-modify-write. The
+// codes stream in 128-bit loads, two per thread at a time, so that enough of
+// them are in flight to keep DRAM busy.
+__device__ __forceinline__ void pos_store(uint32_t c, int64_t p, uint32_t rlo, uint32_t rhi,
+                                          int32_t *__restrict__ pos_src,
+                                          int32_t *__restrict__ pos_dst) {
+    const uint32_t r = c >> 1;
+    if (r >= rlo && r < rhi) {
+        if (c & 1u) pos_dst[r] = (int32_t)p;
+        else pos_src[r] = (int32_t)p;
+    }
+}
+
 __global__ void k_pos_scatter(const uint32_t *__restrict__ codes, int64_t n2, uint32_t rlo,
                               uint32_t rhi, int32_t *__restrict__ pos_src,
                               int32_t *__restrict__ pos_dst) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = __ldcs(codes + p);  // streamed: evict first, keep L2 for the stores
-        const uint32_t r = c >> 1;
-        if (r >= rlo && r < rhi) {
-            if (c & 1u) pos_dst[r] = (int32_t)p;
-            else pos_src[r] = (int32_t)p;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    // whole uint4 groups of codes (none if the array is not 16-byte aligned)
+    const int64_t nv = (reinterpret_cast<uintptr_t>(codes) & 15) ? 0 : n2 / 4;
+    const uint4 *cv = reinterpret_cast<const uint4 *>(codes);
+    for (int64_t v = tid; v < nv; v += 2 * nthreads) {
+        // streamed: evict first, keep L2 for the stores
+        const uint4 a = __ldcs(cv + v);
+        const bool two = v + nthreads < nv;
+        const uint4 b = two ? __ldcs(cv + v + nthreads) : make_uint4(0, 0, 0, 0);
+        const int64_t pa = 4 * v, pb = 4 * (v + nthreads);
+        pos_store(a.x, pa, rlo, rhi, pos_src, pos_dst);
+        pos_store(a.y, pa + 1, rlo, rhi, pos_src, pos_dst);
+        pos_store(a.z, pa + 2, rlo, rhi, pos_src, pos_dst);
+        pos_store(a.w, pa + 3, rlo, rhi, pos_src, pos_dst);
+        if (two) {
+            pos_store(b.x, pb, rlo, rhi, pos_src, pos_dst);
+            pos_store(b.y, pb + 1, rlo, rhi, pos_src, pos_dst);
+            pos_store(b.z, pb + 2, rlo, rhi, pos_src, pos_dst);
+            pos_store(b.w, pb + 3, rlo, rhi, pos_src, pos_dst);
         }
     }
+    for (int64_t p = 4 * nv + tid; p < n2; p += nthreads)
+        pos_store(__ldcs(codes + p), p, rlo, rhi, pos_src, pos_dst);
 }
 
 // Pair list element k (one edge of the node pair (centre, pkey[k]), in rank
