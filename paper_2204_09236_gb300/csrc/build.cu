@@ -497,8 +497,8 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
               n, g.off);
     exclusive_scan_low_bit(codes, g.cin, n2, s);
     TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
-    // both position arrays take 8 bytes per rank: at most 96 MB of them per pass
-    const int64_t ranks_per_pass = (int64_t)12 << 20;
+    // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
+    const int64_t ranks_per_pass = (int64_t)8 << 20;
     for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
         TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
                   (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);

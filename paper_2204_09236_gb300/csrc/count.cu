@@ -150,25 +150,25 @@ __device__ __forceinline__ void flush_star_pair(const unsigned long long *sacc,
     }
 }
 
-// LO: lo_r = lo(r) comes from k_window_lo; otherwise it is found here.
-template <int D3, bool LO>
+// The contributions of entry r (direction D3), its window bounds searched
+// here.
+template <int D3>
 __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta, int32_t r,
-                                                int64_t tr, int32_t u, int2 lr, int32_t lo_r,
+                                                int64_t tr, int32_t u, int2 lr,
                                                 unsigned long long *sacc) {
     const int64_t *__restrict__ tt = g.tt;
     const int32_t seg_b = g.off[u], seg_end = g.off[u + 1];
     // W(r) and F(r) bounds from the neighbouring entries of S_u (local reads);
     // the same-neighbour links are followed only when they land inside.
-    const bool wnd_back =
-        LO ? lr.x >= lo_r : lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
+    const bool wnd_back = lr.x >= 0 && r > seg_b && tr - tt[r - 1] <= delta;
     // the next same-neighbour entry lies in F(r) exactly when it is within delta
     const bool wnd_fwd = lr.y >= 0 && tt[lr.y] - tr <= delta;
     if (!wnd_back && !wnd_fwd) return;
     const int64_t cin_end = g.cin[seg_end];
     const int64_t cin_r = g.cin[r];
     if (wnd_back) {
-        const int32_t lo = LO ? lo_r : gallop_lo(tt, seg_b, r, tr - delta);
-        if (LO || lr.x >= lo) {
+        const int32_t lo = gallop_lo(tt, seg_b, r, tr - delta);
+        if (lr.x >= lo) {
             // per direction d of the run entries: n_d (count), c2s_{d,d'} (pairs),
             // X_{d,d'} (d' entries strictly between a and r), Y_{d,d'} (d' entries
             // before b, as a prefix); kept in scalars so they stay in registers
@@ -260,6 +260,14 @@ __device__ __forceinline__ void star_pair_entry(const DevGraph &g, int64_t delta
 // p: the F terms of all entries are produced here, by the entries that
 // follow them, and an entry whose predecessor is outside its window does
 // nothing at all.
+// Its counts go to the calling lane's copy of the 32 cells: cell i at
+// lane_cells[i * SP_COPIES] (see k_star_pair_list).
+constexpr int SP_COPIES = 33;  // 32 lane copies per cell, padded against bank conflicts
+
+__device__ __forceinline__ void lane_add(unsigned long long *lane_cells, int i, uint64_t v) {
+    if (v) atomicAdd(&lane_cells[i * SP_COPIES], (unsigned long long)v);
+}
+
 __device__ __forceinline__ void star_pair_back_active(const DevGraph &g, int64_t delta, int32_t r,
                                                       int2 lr, int32_t lo,
                                                       unsigned long long *sacc) {
@@ -312,18 +320,18 @@ __device__ __forceinline__ void star_pair_back_active(const DevGraph &g, int64_t
 #pragma unroll
             for (int d2 = 0; d2 < 2; d2++) {
                 const uint64_t sp = c2s[d1][d2];
-                add_cell(sacc, IX(d1, d2, D3), sp);                                 // Pair
-                add_cell(sacc, 16 + IX(d1, d2, D3), X[d1][d2] - sp);                // Star-II
+                lane_add(sacc, IX(d1, d2, D3), sp);                                 // Pair
+                lane_add(sacc, 16 + IX(d1, d2, D3), X[d1][d2] - sp);                // Star-II
                 const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;     // C_d1(lo)
-                add_cell(sacc, 8 + IX(d1, d2, D3), Yp[d2][d1] - n[d2] * base - sp);  // Star-I
-                add_cell(sacc, 24 + IX(d1, d2, D3), 0 - sp);                        // Star-III
+                lane_add(sacc, 8 + IX(d1, d2, D3), Yp[d2][d1] - n[d2] * base - sp);  // Star-I
+                lane_add(sacc, 24 + IX(d1, d2, D3), 0 - sp);                        // Star-III
             }
         const int64_t after_in = cin_end - (cin_r + D3);
         const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
 #pragma unroll
         for (int d1 = 0; d1 < 2; d1++) {
-            add_cell(sacc, 24 + IX(d1, D3, 0), n[d1] * (uint64_t)after_o);
-            add_cell(sacc, 24 + IX(d1, D3, 1), n[d1] * (uint64_t)after_in);
+            lane_add(sacc, 24 + IX(d1, D3, 0), n[d1] * (uint64_t)after_o);
+            lane_add(sacc, 24 + IX(d1, D3, 1), n[d1] * (uint64_t)after_in);
         }
     }
     {
@@ -346,34 +354,25 @@ __device__ __forceinline__ void star_pair_back_active(const DevGraph &g, int64_t
         const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
 #pragma unroll
         for (int d2 = 0; d2 < 2; d2++) {
-            add_cell(sacc, 24 + IX(Dp, d2, 0), 0 - f[d2] * (uint64_t)after_o);
-            add_cell(sacc, 24 + IX(Dp, d2, 1), 0 - f[d2] * (uint64_t)after_in);
+            lane_add(sacc, 24 + IX(Dp, d2, 0), 0 - f[d2] * (uint64_t)after_o);
+            lane_add(sacc, 24 + IX(Dp, d2, 1), 0 - f[d2] * (uint64_t)after_in);
         }
     }
 }
 
 // Star/Pair contributions of the entries [begin, end), visited by threads
-// tid, tid + nthreads, ...; with LO the window starts are read from wlo, and
-// only the back-active entries (lk.x >= lo(r), a few percent) do any work.
-template <bool LO>
+// tid, tid + nthreads, ..., each finding its own window bounds.
 __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta, int64_t begin,
                                                 int64_t end, int64_t tid, int64_t nthreads,
-                                                const int32_t *__restrict__ wlo,
                                                 unsigned long long *sacc) {
     for (int64_t i = begin + tid; i < end; i += nthreads) {
         const int32_t r = (int32_t)i;
-        if constexpr (LO) {
-            const int2 lr = g.lk[r];
-            const int32_t lo_r = wlo[r];
-            if (lr.x >= lo_r) star_pair_back_active(g, delta, r, lr, lo_r, sacc);
-        } else {
-            const int64_t tr = g.tt[r];
-            const uint32_t nbr = g.tn[r].x;
-            const int32_t u = g.tc[r];
-            const int2 lr = g.lk[r];
-            if (dir_of(nbr)) star_pair_entry<1, false>(g, delta, r, tr, u, lr, 0, sacc);
-            else star_pair_entry<0, false>(g, delta, r, tr, u, lr, 0, sacc);
-        }
+        const int64_t tr = g.tt[r];
+        const uint32_t nbr = g.tn[r].x;
+        const int32_t u = g.tc[r];
+        const int2 lr = g.lk[r];
+        if (dir_of(nbr)) star_pair_entry<1>(g, delta, r, tr, u, lr, sacc);
+        else star_pair_entry<0>(g, delta, r, tr, u, lr, sacc);
     }
 }
 
@@ -434,28 +433,36 @@ __global__ void __launch_bounds__(THREADS, 5)
     k_star_pair_list(const DevGraph g, int64_t delta, const int32_t *__restrict__ wlo,
                      const int32_t *__restrict__ act, const int32_t *__restrict__ nact_ptr,
                      unsigned long long *__restrict__ cells) {
-    __shared__ unsigned long long sacc[32];
-    if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
+    // one copy of the 32 cells per lane index (shared by the block's warps),
+    // so the lanes of a warp never add to the same word
+    __shared__ unsigned long long sacc[32 * SP_COPIES];
+    for (int i = threadIdx.x; i < 32 * SP_COPIES; i += blockDim.x) sacc[i] = 0;
     __syncthreads();
     const int32_t nact = *nact_ptr;
+    unsigned long long *mine = sacc + (threadIdx.x & 31);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nact;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = act[i];
-        star_pair_back_active(g, delta, r, g.lk[r], wlo[r], sacc);
+        star_pair_back_active(g, delta, r, g.lk[r], wlo[r], mine);
     }
     __syncthreads();
-    flush_star_pair(sacc, cells);
+    if (threadIdx.x < 32) {
+        const int c = threadIdx.x;
+        unsigned long long v = 0;
+        for (int k = 0; k < 32; k++) v += sacc[c * SP_COPIES + k];
+        if (v) atomicAdd(&cells[c < 8 ? 24 + c : c - 8], v);
+    }
 }
 
-template <bool LO>
+// The Star/Pair sweep without scratch (window bounds searched per entry).
 __global__ void __launch_bounds__(THREADS, 5)
     k_star_pair(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-                const int32_t *__restrict__ wlo, unsigned long long *__restrict__ cells) {
+                unsigned long long *__restrict__ cells) {
     __shared__ unsigned long long sacc[32];
     if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
     __syncthreads();
-    star_pair_range<LO>(g, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                        (int64_t)gridDim.x * blockDim.x, wlo, sacc);
+    star_pair_range(g, delta, begin, end, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                    (int64_t)gridDim.x * blockDim.x, sacc);
     __syncthreads();
     flush_star_pair(sacc, cells);
 }
@@ -988,8 +995,7 @@ __global__ void __launch_bounds__(THREADS)
         if (it.kind == 0) {
             if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
             __syncthreads();
-            star_pair_range<false>(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, nullptr,
-                                   sacc);
+            star_pair_range(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
             __syncthreads();
             flush_star_pair(sacc, cells);
         } else {
@@ -1046,8 +1052,7 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     }
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        TM_LAUNCH(k_star_pair<false>, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end,
-                  nullptr, dev_cells);
+        TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
     }
     {
         PhaseTimer pt(TM_PH_TRI, s);
@@ -1107,8 +1112,7 @@ void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *
     int64_t blocks = (n + THREADS - 1) / THREADS;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    TM_LAUNCH(k_star_pair<false>, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n,
-              nullptr, dev_cells);
+    TM_LAUNCH(k_star_pair, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_tri, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, dev_cells);
     TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
 }
