@@ -522,10 +522,32 @@ __device__ __forceinline__ bool pair_counts_hashed(const DevGraph &g, uint64_t k
         return true;
     }
     if (run.x == run.y) return false;
-    const int32_t k0 = lower_rank(g.pl, run.x, run.y, rank_lo);
-    const int32_t k1 = lower_rank(g.pl, k0, run.y, rank_hi);
+    // the three lower bounds (rank_lo, rank_hi, at) searched over the whole
+    // run side by side, so that their loads are in flight together; the
+    // item's bound is then clamped into [k0, k1]
+    int32_t b0 = run.x, e0 = run.y, b1 = run.x, e1 = run.y, b2 = run.x, e2 = run.y;
+    while (b0 < e0 || b1 < e1 || b2 < e2) {
+        const int32_t m0 = b0 + ((e0 - b0) >> 1), m1 = b1 + ((e1 - b1) >> 1),
+                      m2 = b2 + ((e2 - b2) >> 1);
+        const int32_t r0 = b0 < e0 ? g.pl[m0].x : 0;
+        const int32_t r1 = b1 < e1 ? g.pl[m1].x : 0;
+        const int32_t r2 = b2 < e2 ? g.pl[m2].x : 0;
+        if (b0 < e0) {
+            if (r0 < rank_lo) b0 = m0 + 1;
+            else e0 = m0;
+        }
+        if (b1 < e1) {
+            if (r1 < rank_hi) b1 = m1 + 1;
+            else e1 = m1;
+        }
+        if (b2 < e2) {
+            if (r2 < at) b2 = m2 + 1;
+            else e2 = m2;
+        }
+    }
+    const int32_t k0 = b0, k1 = b1 > k0 ? b1 : k0;
     if (k0 == k1) return false;
-    const int32_t ks = lower_rank(g.pl, k0, k1, at);
+    const int32_t ks = b2 < k0 ? k0 : (b2 > k1 ? k1 : b2);
     const int32_t c0 = g.pl[k0].y, cs = g.pl[ks].y, c1 = g.pl[k1].y;
     c.nb = ks - k0;
     c.na = k1 - ks;
