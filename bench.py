@@ -44,7 +44,7 @@ ALGO_BYTES = {"star_pair": 32, "tri": 48, "time_sort": 16, "incident": 48, "pair
 # full workload, from one ncu capture of dram__bytes_read.sum +
 # dram__bytes_write.sum (profiles/count_kernels_dram_large_60M.md); None until
 # captured for the current kernels
-TRI_TRAFFIC = {}
+TRI_TRAFFIC = {"large": 9.06e9 + 0.302e9 + 4.00e9 + 0.084e9}
 
 WORKLOADS = {
     "large": dict(desc="large: 2.5M nodes, 60M edges, Zipf(2.0) degree law, out-degree cap 2e5, "
