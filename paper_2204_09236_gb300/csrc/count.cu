@@ -376,13 +376,42 @@ __device__ __forceinline__ void star_pair_range(const DevGraph &g, int64_t delta
     }
 }
 
+// First position p in [a, r] with tt[p] >= bound, searching forward from a
+// with first step `step` (a guess of the distance); tt[r] >= bound holds.
+__device__ __forceinline__ int32_t gallop_fwd(const int64_t *__restrict__ tt, int32_t a, int32_t r,
+                                              int64_t bound, int32_t step) {
+    if (tt[a] >= bound) return a;
+    int32_t lo = a, hi = r;  // tt[lo] < bound <= tt[hi]
+    while (true) {
+        const int32_t p = lo + step;
+        if (p >= r) break;
+        if (tt[p] >= bound) {
+            hi = p;
+            break;
+        }
+        lo = p;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (tt[mid] >= bound) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
 // lo(r) for every entry r in [begin, end): the first entry of W(r), r itself
-// when the window is empty. Consecutive entries share their centre and most of
-// their window, so the backward searches of a warp read the same lines.
+// when the window is empty. Each warp takes WLO_GROUPS consecutive groups of
+// 32 entries; a lane's entry in group g is 32 entries after its entry in
+// group g-1, and lo never decreases along one centre, so when both are of the
+// same centre the lane searches forwards from its previous lo (the window has
+// slid by about 32 entries) instead of backwards from r.
 // With `act`, the back-active entries (lk.x >= lo(r): a few percent, and the
 // only ones with Star/Pair contributions) are listed there as well, each warp
 // gathering them in shared memory and reserving space 32 at a time. The
 // order of the list is immaterial: every entry adds its counts.
+constexpr int WLO_GROUPS = 16;
+
 __global__ void __launch_bounds__(THREADS)
     k_window_lo(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
                 int32_t *__restrict__ wlo, int32_t *__restrict__ act,
@@ -390,33 +419,44 @@ __global__ void __launch_bounds__(THREADS)
     __shared__ int32_t buf[THREADS / 32][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *wb = buf[warp];
-    int cnt = 0;  // entries held in wb (warp-uniform, < 32 between steps)
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < end;
-         base += nthreads) {
-        const int64_t i = base + lane;
-        bool active = false;
-        if (i < end) {
-            const int32_t r = (int32_t)i;
-            const int64_t tr = g.tt[r];
-            const int32_t sb = g.off[g.tc[r]];
-            int32_t lo = r;
-            if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
-            wlo[r] = lo;
-            active = act != nullptr && lo < r && g.lk[r].x >= lo;
-        }
-        if (act == nullptr) continue;
-        const unsigned bal = __ballot_sync(0xffffffffu, active);
-        if (active) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
-        cnt += __popc(bal);
-        __syncwarp();
-        if (cnt >= 32) {
-            int32_t first = 0;
-            if (lane == 0) first = atomicAdd(nact, 32);
-            first = __shfl_sync(0xffffffffu, first, 0);
-            act[first + lane] = wb[cnt - 32 + lane];
-            cnt -= 32;
+    int cnt = 0;  // entries held in wb (warp-uniform, < 32 between groups)
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int64_t CHUNK = 32 * WLO_GROUPS;
+    for (int64_t c0 = begin + wid * CHUNK; c0 < end; c0 += nwarps * CHUNK) {
+        int32_t prev_u = -1, prev_lo = 0;
+        for (int gi = 0; gi < WLO_GROUPS; gi++) {
+            const int64_t i = c0 + gi * 32 + lane;
+            bool active = false;
+            if (i < end) {
+                const int32_t r = (int32_t)i;
+                const int64_t tr = g.tt[r];
+                const int32_t u = g.tc[r];
+                int32_t lo = r;
+                if (u == prev_u) {
+                    lo = gallop_fwd(g.tt, prev_lo, r, tr - delta, 32);
+                } else {
+                    const int32_t sb = g.off[u];
+                    if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
+                }
+                prev_u = u;
+                prev_lo = lo;
+                wlo[r] = lo;
+                active = act != nullptr && lo < r && g.lk[r].x >= lo;
+            }
+            if (act == nullptr) continue;
+            const unsigned bal = __ballot_sync(0xffffffffu, active);
+            if (active) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+            cnt += __popc(bal);
             __syncwarp();
+            if (cnt >= 32) {
+                int32_t first = 0;
+                if (lane == 0) first = atomicAdd(nact, 32);
+                first = __shfl_sync(0xffffffffu, first, 0);
+                act[first + lane] = wb[cnt - 32 + lane];
+                cnt -= 32;
+                __syncwarp();
+            }
         }
     }
     if (act != nullptr && cnt > 0) {
