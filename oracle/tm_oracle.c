@@ -263,8 +263,8 @@ static void alg1_first_edge(orc_graph *g, int64_t i, int64_t se, int64_t delta,
 
 /* Body of Algorithm 2 for one e_i = S_u[i]. For every e_j after e_i with
  * t_j <= t_i + delta and a different neighbour, scan E_(v,w) from the first
- * edge with t >= t_j - delta (the "implementation trick" that limits xi to the
- * edges within delta) and classify each e_k by its place in the total order. */
+ * edge with t >= t_j - delta (Sec. IV-B's shortcut, which limits xi to the edges
+ * within delta) and classify each e_k by its place in the total order. */
 static void alg2_first_edge(const orc_graph *g, int64_t i, int64_t se, int64_t delta,
                             uint64_t *tri) {
     const s_entry *S = g->S;

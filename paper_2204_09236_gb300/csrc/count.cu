@@ -28,17 +28,26 @@
 //
 // Tri (Alg. 2): only type II is computed. Each triangle instance adds exactly
 // one count to a type-I, a type-II and a type-III cell of the same class
-// (Sec. IV-B, "counted three times"), so the type-I and type-III cells are
-// filled from type II by the rotation identity
+// (Sec. IV-B counts each instance three times), so the type-I and type-III
+// cells are filled from type II by the rotation identity
 //   Tri[II,di,dj,dk] = Tri[I,!dk,!dj,!di] = Tri[III,!di,dk,dj].
 // Type II at centre u with later u-edge e_j = (u, w): pairs e_i < e_k < e_j
 // with e_i = (u, x) in W_u(e_j) and e_k = (x, w), which then lies in
 // W_w(e_j). So for each edge e_j the type-II triangles at BOTH of its
 // endpoints are the same-neighbour matches between the two endpoint windows
 // W_u(e_j) and W_w(e_j): a match (a in W_u, k in W_w) with a < k is centred at
-// u, one with k < a at w. k_tri visits each edge once, enumerates the smaller
-// window and finds the matches in the bigger one through the pair list
-// (hash lookup of E_(big, x), binary search on rank).
+// u, one with k < a at w. Each edge is joined once, at its source entry: the
+// smaller window is enumerated and the matches are found in the bigger one
+// through the pair list (hash lookup of E_(big, x), binary search on rank).
+// k_tri_jobs lists the edges whose two windows are both non-empty and
+// k_tri_join runs their joins; k_tri does both in one kernel without scratch.
+//
+// Star/Pair work lists: an entry has W(r) terms only if its previous
+// same-neighbour entry p lies in W(r) (it is "back-active"), and F(p) holds a
+// same-neighbour entry exactly when p's next one, r, is back-active with p.
+// So k_window_lo lists the back-active entries while it finds every lo(r),
+// and k_star_pair_list makes each of them produce its own W terms and its
+// predecessor's F term; k_star_pair does the same per entry without scratch.
 #include "tm_internal.cuh"
 
 namespace tmi {
@@ -519,17 +528,6 @@ __device__ __forceinline__ int2 find_pair(const PairSlot *__restrict__ H, uint32
         h = (h + 1) & mask;
     }
     return make_int2(0, 0);
-}
-
-// First index in [b, e) with pl[].x >= x.
-__device__ __forceinline__ int32_t lower_rank(const int2 *__restrict__ pl, int32_t b, int32_t e,
-                                              int32_t x) {
-    while (b < e) {
-        int32_t mid = b + ((e - b) >> 1);
-        if (pl[mid].x < x) b = mid + 1;
-        else e = mid;
-    }
-    return b;
 }
 
 // Edges of E_(big, x) inside [rank_lo, rank_hi), split at rank `at`:
