@@ -101,6 +101,10 @@ int tm_count_raw(const tm_graph *g, int64_t delta, uint64_t star[24], uint64_t p
  * to dev_cells, a device uint64[56] owned by the caller. Returns as soon as
  * the work is enqueued; the cells are valid once the stream reaches that
  * point. Must not overlap another count that uses the same dev_cells.
+ * Like tm_count, tm_count_raw and tm_count_select, it borrows about 36 bytes
+ * per edge of scratch (window starts, the list of entries with Star/Pair
+ * terms, the Tri joins) from the device's stream-ordered memory pool for the
+ * duration of the count; tm_count_batch and tm_count_noalloc borrow none.
  */
 int tm_count_async(const tm_graph *g, int64_t delta, void *stream, uint64_t *dev_cells);
 
