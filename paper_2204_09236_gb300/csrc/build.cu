@@ -3,7 +3,8 @@
 // Steps (one stream):
 //   1. validate ids / self-loops, find n, min t, max t          (k_validate)
 //   2. stable radix sort of the edges by t - t_min -> rank order  (ties keep
-//      the edge-id order: the (t, edge id) total order)
+//      the edge-id order: the (t, edge id) total order); skipped when the
+//      input is already in time order
 //   3. incident entries of every centre, stable radix sort by centre: S_u in
 //      (t, id) order for every u (Table 1; "get S_u" in Alg. 1 and Alg. 2)
 //   4. in-count prefix over the entries (cin), entry positions of each edge
@@ -25,14 +26,14 @@ struct Validation {
     int32_t max_id;
     int32_t bad_neg;
     int32_t bad_loop;
-    int32_t pad;
+    int32_t unsorted;  // some t[e] < t[e-1]: the input is not in time order
     long long tmin;
     long long tmax;
 };
 
 __global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                            const int64_t *__restrict__ t, int64_t m, Validation *v) {
-    int32_t mx = -1, neg = 0, loop = 0;
+    int32_t mx = -1, neg = 0, loop = 0, uns = 0;
     long long tmn = LLONG_MAX, tmx = LLONG_MIN;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -43,11 +44,13 @@ __global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__res
         long long x = t[e];
         tmn = min(tmn, x);
         tmx = max(tmx, x);
+        if (e > 0) uns |= x < t[e - 1];
     }
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         neg |= __shfl_xor_sync(0xffffffffu, neg, o);
         loop |= __shfl_xor_sync(0xffffffffu, loop, o);
+        uns |= __shfl_xor_sync(0xffffffffu, uns, o);
         tmn = min(tmn, __shfl_xor_sync(0xffffffffu, tmn, o));
         tmx = max(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
     }
@@ -55,6 +58,7 @@ __global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__res
         atomicMax(&v->max_id, mx);
         if (neg) atomicOr(&v->bad_neg, 1);
         if (loop) atomicOr(&v->bad_loop, 1);
+        if (uns) atomicOr(&v->unsorted, 1);
         atomicMin(&v->tmin, tmn);
         atomicMax(&v->tmax, tmx);
     }
@@ -64,6 +68,7 @@ __global__ void k_validation_init(Validation *v) {
     v->max_id = -1;
     v->bad_neg = 0;
     v->bad_loop = 0;
+    v->unsorted = 0;
     v->tmin = LLONG_MAX;
     v->tmax = LLONG_MIN;
 }
@@ -435,27 +440,37 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
 // codes. Then off, cin and the position arrays. Scratch buffers
 // (and, through release_inputs, the edge arrays) are released as soon as the
 // kernels after them no longer read them.
+// Input already in time order (t non-decreasing along the edge ids, as
+// temporal-graph files usually come): its order is the (t, edge id) order, so
+// the time sort is skipped.
 template <typename K, typename Release>
 void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
-                            int keybits, int nbits, Release release_inputs,
+                            int keybits, int nbits, bool time_ordered, Release release_inputs,
                             cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m, n = g.n;
     K *sk;
     uint64_t *sv;
-    K *k1 = dev_alloc_n<K>(m, s), *k2 = dev_alloc_n<K>(m, s);
-    uint64_t *v1 = dev_alloc_n<uint64_t>(m, s), *v2 = dev_alloc_n<uint64_t>(m, s);
+    K *k1 = dev_alloc_n<K>(m, s);
+    uint64_t *v1 = dev_alloc_n<uint64_t>(m, s);
     {
         PhaseTimer pt(TM_PH_TIME_SORT, s);
         TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin, k1,
                   v1);
         release_inputs();
-        if constexpr (sizeof(K) == 4)
-            radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-        else
-            radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-        // the pair not holding the result is free now
-        dev_free(sk == k1 ? k2 : k1, s);
-        dev_free(sv == v1 ? v2 : v1, s);
+        if (time_ordered) {
+            sk = k1;
+            sv = v1;
+        } else {
+            K *k2 = dev_alloc_n<K>(m, s);
+            uint64_t *v2 = dev_alloc_n<uint64_t>(m, s);
+            if constexpr (sizeof(K) == 4)
+                radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+            else
+                radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+            // the pair not holding the result is free now
+            dev_free(sk == k1 ? k2 : k1, s);
+            dev_free(sv == v1 ? v2 : v1, s);
+        }
     }
     PhaseTimer pt(TM_PH_INCIDENT, s);
     uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);
@@ -612,10 +627,13 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     // 2-4. rank order, then S_u for every centre
     const int keybits = bits_for(span);
     const int nbits = bits_for((uint64_t)(n - 1));
+    const bool time_ordered = hv.unsorted == 0;
     if (keybits <= 32)
-        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, release_inputs, s);
+        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, time_ordered,
+                                         release_inputs, s);
     else
-        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, release_inputs, s);
+        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, time_ordered,
+                                         release_inputs, s);
 
     // 5-6. pair list, same-neighbour links, hash
     {
