@@ -2,8 +2,9 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. The CUDA path never does, and the two
-share no code: this package wraps ``tm_oracle.c`` (plain C, single thread),
-which implements Algorithm 1 and Algorithm 2 of arXiv 2204.09236 literally,
+share no code: this package wraps ``tm_oracle.c`` (plain C),
+which implements Algorithm 1 and Algorithm 2 of arXiv 2204.09236 literally
+(single thread, or spread over host threads by ranges of first edges),
 the brute-force definitions (Def. 2, Def. 3), and the 36-class layout.
 
 Counter layout (numpy uint64 arrays):
@@ -37,8 +38,8 @@ def build(force: bool = False) -> Path:
     _BUILD.mkdir(exist_ok=True)
     if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _BUILD / f"liboracle.{os.getpid()}.so"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(tmp),
-                               str(_SRC)])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o",
+                               str(tmp), str(_SRC)])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -53,6 +54,7 @@ def _bind(lib):
     lib.orc_count.argtypes = [P, i64, P, P, P]
     lib.orc_count_entries.argtypes = [P, i64, P, i64, P, P, P]
     lib.orc_count_centre.argtypes = [P, i64, ctypes.c_int32, P, P, P]
+    lib.orc_count_mt.argtypes = [P, i64, ctypes.c_int32, i64, P, P, P]
     lib.orc_num_nodes.restype = i64
     lib.orc_num_nodes.argtypes = [P]
     lib.orc_num_entries.restype = i64
@@ -117,6 +119,19 @@ class Graph:
         s, p, q = _cells()
         if self._lib.orc_count(self._h, int(delta), _ptr(s), _ptr(p), _ptr(q)) != 0:
             raise ValueError("oracle: delta must be >= 0")
+        return s, p, q
+
+    def count_mt(self, delta, threads=None, chunk=4096):
+        """As count, on `threads` host threads (default: every core): the
+        first edges are cut into chunks of `chunk` S_u positions that threads
+        take dynamically (Sec. IV-C's inter- and intra-node split). Returns
+        (star, pair, tri), equal to count's."""
+        threads = int(threads or os.cpu_count() or 1)
+        s, p, q = _cells()
+        rc = self._lib.orc_count_mt(self._h, int(delta), threads, int(chunk), _ptr(s), _ptr(p),
+                                    _ptr(q))
+        if rc != 0:
+            raise ValueError(f"oracle count_mt: rc={rc} (bad argument or out of memory)")
         return s, p, q
 
     def count_entries(self, delta, idx):

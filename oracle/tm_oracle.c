@@ -32,6 +32,8 @@
  *   - dir_k of a triangle is relative to v = e_i.v (Sec. IV-B definition).
  *   - Self-loops are rejected (all workloads have u != v).
  */
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -71,10 +73,28 @@ typedef struct {
     int64_t *pkey; /* sorted keys lo*n + hi */
     int64_t *poff; /* npairs+1 */
     p_entry *P;    /* m, grouped by pair, sorted by (t, id) */
-    /* scratch for the HashMaps of Algorithm 1 (direct addressing + reset list) */
+} orc_graph;
+
+/* The HashMaps m_in / m_out of Algorithm 1 (direct addressing by node id,
+ * with the list of touched keys for HashMap.Init()). Each thread of
+ * orc_count_mt has its own. */
+typedef struct {
     int64_t *map_in, *map_out;
     int32_t *touched;
-} orc_graph;
+} alg1_maps;
+
+static int maps_init(alg1_maps *h, int32_t n, int64_t m) {
+    h->map_in = calloc((size_t)n + 1, sizeof(int64_t));
+    h->map_out = calloc((size_t)n + 1, sizeof(int64_t));
+    h->touched = malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    return h->map_in && h->map_out && h->touched;
+}
+
+static void maps_free(alg1_maps *h) {
+    free(h->map_in);
+    free(h->map_out);
+    free(h->touched);
+}
 
 /* (t, id) total order */
 static int before(int64_t ta, int32_t ia, int64_t tb, int32_t ib) {
@@ -108,9 +128,6 @@ void orc_free(orc_graph *g) {
     free(g->pkey);
     free(g->poff);
     free(g->P);
-    free(g->map_in);
-    free(g->map_out);
-    free(g->touched);
     free(g);
 }
 
@@ -134,10 +151,7 @@ orc_graph *orc_build(int64_t m, const int32_t *src, const int32_t *dst, const in
     g->n = n;
     g->off = calloc((size_t)n + 1, sizeof(int64_t));
     g->S = malloc(sizeof(s_entry) * (size_t)(2 * m + 1));
-    g->map_in = calloc((size_t)n + 1, sizeof(int64_t));
-    g->map_out = calloc((size_t)n + 1, sizeof(int64_t));
-    g->touched = malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
-    if (!g->off || !g->S || !g->map_in || !g->map_out || !g->touched) {
+    if (!g->off || !g->S) {
         orc_free(g);
         return NULL;
     }
@@ -223,8 +237,8 @@ static void pair_range(const orc_graph *g, int32_t v, int32_t w, int64_t *b, int
  * centre segment [sb, se)). m_in / m_out count the second-edge candidates
  * strictly between e1 and the current e3, per neighbour; #e_in / #e_out count
  * them over all neighbours. */
-static void alg1_first_edge(orc_graph *g, int64_t i, int64_t se, int64_t delta,
-                            uint64_t *star, uint64_t *pair) {
+static void alg1_first_edge(const orc_graph *g, alg1_maps *h, int64_t i, int64_t se,
+                            int64_t delta, uint64_t *star, uint64_t *pair) {
     const s_entry *S = g->S;
     const s_entry e1 = S[i];
     int64_t n_in = 0, n_out = 0;
@@ -233,29 +247,29 @@ static void alg1_first_edge(orc_graph *g, int64_t i, int64_t se, int64_t delta,
         const s_entry e3 = S[j];
         if (e3.t - e1.t > delta) break;
         if (e3.v == e1.v) {
-            PAIR(e1.dir, IN, e3.dir) += g->map_in[e1.v];
-            PAIR(e1.dir, O, e3.dir) += g->map_out[e1.v];
-            STAR(T_II, e1.dir, IN, e3.dir) += n_in - g->map_in[e1.v];
-            STAR(T_II, e1.dir, O, e3.dir) += n_out - g->map_out[e1.v];
+            PAIR(e1.dir, IN, e3.dir) += h->map_in[e1.v];
+            PAIR(e1.dir, O, e3.dir) += h->map_out[e1.v];
+            STAR(T_II, e1.dir, IN, e3.dir) += n_in - h->map_in[e1.v];
+            STAR(T_II, e1.dir, O, e3.dir) += n_out - h->map_out[e1.v];
         } else {
-            STAR(T_I, e1.dir, IN, e3.dir) += g->map_in[e3.v];
-            STAR(T_I, e1.dir, O, e3.dir) += g->map_out[e3.v];
-            STAR(T_III, e1.dir, IN, e3.dir) += g->map_in[e1.v];
-            STAR(T_III, e1.dir, O, e3.dir) += g->map_out[e1.v];
+            STAR(T_I, e1.dir, IN, e3.dir) += h->map_in[e3.v];
+            STAR(T_I, e1.dir, O, e3.dir) += h->map_out[e3.v];
+            STAR(T_III, e1.dir, IN, e3.dir) += h->map_in[e1.v];
+            STAR(T_III, e1.dir, O, e3.dir) += h->map_out[e1.v];
         }
-        if (g->map_in[e3.v] == 0 && g->map_out[e3.v] == 0) g->touched[ntouched++] = e3.v;
+        if (h->map_in[e3.v] == 0 && h->map_out[e3.v] == 0) h->touched[ntouched++] = e3.v;
         if (e3.dir == IN) {
-            g->map_in[e3.v] += 1;
+            h->map_in[e3.v] += 1;
             n_in += 1;
         } else {
-            g->map_out[e3.v] += 1;
+            h->map_out[e3.v] += 1;
             n_out += 1;
         }
     }
     /* HashMap.Init() for the next e1 */
     for (int64_t k = 0; k < ntouched; k++) {
-        g->map_in[g->touched[k]] = 0;
-        g->map_out[g->touched[k]] = 0;
+        h->map_in[h->touched[k]] = 0;
+        h->map_out[h->touched[k]] = 0;
     }
 }
 
@@ -310,16 +324,23 @@ static int32_t centre_of(const orc_graph *g, int64_t i) {
 }
 
 /* All 56 cells for every centre node (Algorithm 1 and Algorithm 2). The
- * counters are accumulated, not cleared. Returns -1 on delta < 0. */
+ * counters are accumulated, not cleared. Returns -1 on delta < 0, -2 when
+ * out of memory. */
 int orc_count(orc_graph *g, int64_t delta, uint64_t *star, uint64_t *pair, uint64_t *tri) {
     if (delta < 0) return -1;
+    alg1_maps h;
+    if (!maps_init(&h, g->n, g->m)) {
+        maps_free(&h);
+        return -2;
+    }
     for (int32_t u = 0; u < g->n; u++) {
         const int64_t sb = g->off[u], se = g->off[u + 1];
         for (int64_t i = sb; i < se; i++) {
-            alg1_first_edge(g, i, se, delta, star, pair);
+            alg1_first_edge(g, &h, i, se, delta, star, pair);
             alg2_first_edge(g, i, se, delta, tri);
         }
     }
+    maps_free(&h);
     return 0;
 }
 
@@ -328,14 +349,21 @@ int orc_count(orc_graph *g, int64_t delta, uint64_t *star, uint64_t *pair, uint6
 int orc_count_entries(orc_graph *g, int64_t delta, const int64_t *idx, int64_t k,
                       uint64_t *star, uint64_t *pair, uint64_t *tri) {
     if (delta < 0) return -1;
+    for (int64_t q = 0; q < k; q++)
+        if (idx[q] < 0 || idx[q] >= 2 * g->m) return -1;
+    alg1_maps h;
+    if (!maps_init(&h, g->n, g->m)) {
+        maps_free(&h);
+        return -2;
+    }
     for (int64_t q = 0; q < k; q++) {
         const int64_t i = idx[q];
-        if (i < 0 || i >= 2 * g->m) return -1;
         const int32_t u = centre_of(g, i);
         const int64_t se = g->off[u + 1];
-        alg1_first_edge(g, i, se, delta, star, pair);
+        alg1_first_edge(g, &h, i, se, delta, star, pair);
         alg2_first_edge(g, i, se, delta, tri);
     }
+    maps_free(&h);
     return 0;
 }
 
@@ -343,12 +371,102 @@ int orc_count_entries(orc_graph *g, int64_t delta, const int64_t *idx, int64_t k
 int orc_count_centre(orc_graph *g, int64_t delta, int32_t u, uint64_t *star, uint64_t *pair,
                      uint64_t *tri) {
     if (delta < 0 || u < 0 || u >= g->n) return -1;
+    alg1_maps h;
+    if (!maps_init(&h, g->n, g->m)) {
+        maps_free(&h);
+        return -2;
+    }
     const int64_t sb = g->off[u], se = g->off[u + 1];
     for (int64_t i = sb; i < se; i++) {
-        alg1_first_edge(g, i, se, delta, star, pair);
+        alg1_first_edge(g, &h, i, se, delta, star, pair);
         alg2_first_edge(g, i, se, delta, tri);
     }
+    maps_free(&h);
     return 0;
+}
+
+/* ------------------------------------------- hierarchical parallel count */
+
+/* orc_count on several host threads: the paper's hierarchical scheme
+ * (Sec. IV-C) with centres shared out dynamically (inter-node) and a high-
+ * degree centre's first edges split into ranges (intra-node). The 2m first
+ * edges of the concatenated S_u lists are cut into chunks of `chunk`
+ * consecutive positions, which may cut one S_u into several chunks; threads
+ * take the next chunk from a shared counter, run the Algorithm 1 and
+ * Algorithm 2 bodies for each first edge of it with their own HashMaps and
+ * their own counters, and the counters are summed at the end. Every first
+ * edge is processed exactly once, and the body of one first edge reads only
+ * the graph, so the sum equals orc_count. */
+typedef struct {
+    const orc_graph *g;
+    int64_t delta, chunk, nchunks;
+    atomic_llong *next;
+    uint64_t cells[56];
+    int status;
+} mt_worker;
+
+static void *mt_run(void *arg) {
+    mt_worker *w = arg;
+    const orc_graph *g = w->g;
+    alg1_maps h;
+    if (!maps_init(&h, g->n, g->m)) {
+        maps_free(&h);
+        w->status = -2;
+        return NULL;
+    }
+    uint64_t *star = w->cells, *pair = w->cells + 24, *tri = w->cells + 32;
+    for (;;) {
+        const int64_t c = atomic_fetch_add(w->next, 1);
+        if (c >= w->nchunks) break;
+        const int64_t b = c * w->chunk;
+        const int64_t e = b + w->chunk < 2 * g->m ? b + w->chunk : 2 * g->m;
+        int32_t u = centre_of(g, b);
+        for (int64_t i = b; i < e; i++) {
+            while (g->off[u + 1] <= i) u++;
+            alg1_first_edge(g, &h, i, g->off[u + 1], w->delta, star, pair);
+            alg2_first_edge(g, i, g->off[u + 1], w->delta, tri);
+        }
+    }
+    maps_free(&h);
+    return NULL;
+}
+
+/* Returns 0, -1 on a bad argument (delta < 0, nthreads < 1, chunk < 1), -2
+ * when out of memory or a thread cannot start. Accumulates like orc_count. */
+int orc_count_mt(orc_graph *g, int64_t delta, int32_t nthreads, int64_t chunk, uint64_t *star,
+                 uint64_t *pair, uint64_t *tri) {
+    if (delta < 0 || nthreads < 1 || chunk < 1) return -1;
+    if (g->m == 0) return 0;
+    mt_worker *w = calloc((size_t)nthreads, sizeof(mt_worker));
+    pthread_t *th = calloc((size_t)nthreads, sizeof(pthread_t));
+    int *started = calloc((size_t)nthreads, sizeof(int));
+    atomic_llong next;
+    atomic_init(&next, 0);
+    int rc = 0;
+    if (!w || !th || !started) rc = -2;
+    for (int32_t k = 0; rc == 0 && k < nthreads; k++) {
+        w[k].g = g;
+        w[k].delta = delta;
+        w[k].chunk = chunk;
+        w[k].nchunks = (2 * g->m + chunk - 1) / chunk;
+        w[k].next = &next;
+        started[k] = pthread_create(&th[k], NULL, mt_run, &w[k]) == 0;
+        if (!started[k]) rc = -2;
+    }
+    for (int32_t k = 0; w && th && started && k < nthreads; k++) {
+        if (!started[k]) continue;
+        pthread_join(th[k], NULL);
+        if (w[k].status) rc = w[k].status;
+    }
+    for (int32_t k = 0; rc == 0 && k < nthreads; k++) {
+        for (int c = 0; c < 24; c++) star[c] += w[k].cells[c];
+        for (int c = 0; c < 8; c++) pair[c] += w[k].cells[24 + c];
+        for (int c = 0; c < 24; c++) tri[c] += w[k].cells[32 + c];
+    }
+    free(w);
+    free(th);
+    free(started);
+    return rc;
 }
 
 /* ------------------------------------------------------ the definitions */

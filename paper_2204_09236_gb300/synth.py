@@ -261,6 +261,16 @@ def trace(seed=SEED_BASE + 5, rate=200.0, seconds=60.0, requery=0.30):
     return arrivals, seeds, sizes, deltas, pick
 
 
+def fingerprint(src, dst, t):
+    """SHA-256 (hex, first 16 digits) of the three input arrays' bytes, so that
+    stored results can name exactly the graph they were computed on."""
+    import hashlib
+    h = hashlib.sha256()
+    for a, dt in ((src, np.int32), (dst, np.int32), (t, np.int64)):
+        h.update(np.ascontiguousarray(a, dt).tobytes())
+    return h.hexdigest()[:16]
+
+
 def random_small(seed, n_nodes, m, t_range, allow_dup=True):
     """Tiny tie-heavy multigraph for brute-force checks."""
     rng = _rng(seed)

@@ -216,6 +216,39 @@ def test_count_entries_partition():
         assert (parts[0][k] + parts[1][k] == full[k]).all()
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_multithreaded_count_equals_definition(seed):
+    """The hierarchical parallel count (Sec. IV-C: centres and, inside one
+    S_u, ranges of first edges shared out over threads) against the
+    definition, with chunks small enough to cut every S_u into pieces."""
+    rng = np.random.default_rng(seed)
+    s, d, t = synth.random_small(3000 + seed, int(rng.integers(3, 9)), int(rng.integers(5, 60)),
+                                 int(rng.integers(1, 15)))
+    G = oracle.Graph(s, d, t)
+    for delta in (0, 2, 5, 100):
+        want = oracle.brute(s, d, t, delta)
+        for threads, chunk in ((1, 1), (2, 3), (3, 7), (5, 1 << 20)):
+            got = G.count_mt(delta, threads=threads, chunk=chunk)
+            for a, b in zip(got, want):
+                assert (a == b).all(), (delta, threads, chunk)
+
+
+def test_multithreaded_count_on_toy_and_tiny():
+    s, d, t = synth.toy_graph()
+    G = oracle.Graph(s, d, t)
+    for threads, chunk in ((4, 1), (3, 5)):
+        for a, b in zip(G.count_mt(10, threads=threads, chunk=chunk), G.count(10)):
+            assert (a == b).all()
+    s, d, t = synth.tiny()
+    G = oracle.Graph(s, d, t)
+    for a, b in zip(G.count_mt(3600, threads=4, chunk=97), G.count(3600)):
+        assert (a == b).all()
+    with pytest.raises(ValueError):
+        G.count_mt(-1)
+    with pytest.raises(ValueError):
+        G.count_mt(10, chunk=0)
+
+
 # ------------------------------------------------------------- closed forms
 
 

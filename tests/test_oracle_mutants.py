@@ -23,17 +23,21 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden", "toy_worked_examples.js
 MUTANTS = {
     # Algorithm 1
     "alg1_window_strict": ("if (e3.t - e1.t > delta) break;", "if (e3.t - e1.t >= delta) break;"),
-    "alg1_drop_star_I_out": ("STAR(T_I, e1.dir, O, e3.dir) += g->map_out[e3.v];", ""),
-    "alg1_star_III_wrong_node": ("STAR(T_III, e1.dir, IN, e3.dir) += g->map_in[e1.v];",
-                                 "STAR(T_III, e1.dir, IN, e3.dir) += g->map_in[e3.v];"),
-    "alg1_pair_transposed": ("PAIR(e1.dir, IN, e3.dir) += g->map_in[e1.v];",
-                             "PAIR(e3.dir, IN, e1.dir) += g->map_in[e1.v];"),
+    "alg1_drop_star_I_out": ("STAR(T_I, e1.dir, O, e3.dir) += h->map_out[e3.v];", ""),
+    "alg1_star_III_wrong_node": ("STAR(T_III, e1.dir, IN, e3.dir) += h->map_in[e1.v];",
+                                 "STAR(T_III, e1.dir, IN, e3.dir) += h->map_in[e3.v];"),
+    "alg1_pair_transposed": ("PAIR(e1.dir, IN, e3.dir) += h->map_in[e1.v];",
+                             "PAIR(e3.dir, IN, e1.dir) += h->map_in[e1.v];"),
     # Algorithm 2
     "alg2_raw_time_order": ("} else if (before(ei.t, ei.id, ek.t, ek.id) && before(ek.t, ek.id, ej.t, ej.id)) {",
                             "} else if (ei.t <= ek.t && ek.t <= ej.t) {"),
     "alg2_dir_k_wrt_w": ("const int dk = ek.src == v ? O : IN;", "const int dk = ek.src == w ? O : IN;"),
     "alg2_type_III_window": ("&& ek.t - ei.t <= delta) {", "&& ek.t - ej.t <= delta) {"),
     "alg2_tri_transposed": ("TRI(T_II, ei.dir, ej.dir, dk)++;", "TRI(T_II, ej.dir, ei.dir, dk)++;"),
+    # the multi-threaded split (Sec. IV-C)
+    "mt_chunk_end_short": ("const int64_t e = b + w->chunk < 2 * g->m ? b + w->chunk : 2 * g->m;",
+                           "const int64_t e = b + w->chunk < 2 * g->m ? b + w->chunk - 1 : 2 * g->m;"),
+    "mt_stale_centre": ("            while (g->off[u + 1] <= i) u++;\n", ""),
     # the definitions
     "brute_star_type": ("const int iso = s12 ? 0 : (s02 ? 1 : 2);", "const int iso = s12 ? 2 : (s02 ? 1 : 0);"),
     "brute_tri_dirk_wrt_u": ("TRI(type, dir_wrt(ei, u), dir_wrt(ej, u), dir_wrt(ek, v))++;",
@@ -78,6 +82,14 @@ def _battery():
                 break
         if failed:
             break
+    # the multi-threaded count, with S_u lists cut into chunks
+    for seed in range(6):
+        s, d, t = synth.random_small(2000 + seed, 5, 30, 6)
+        G = oracle.Graph(s, d, t)
+        b = oracle.brute(s, d, t, 3)
+        if not all((x == y).all() for x, y in zip(G.count_mt(3, threads=3, chunk=4), b)):
+            failed.append("multi-threaded count vs definition")
+            break
     # closed form: one static triangle counted once
     s, d, t = np.array([0, 1, 0]), np.array([1, 2, 2]), np.array([0, 1, 2])
     merged, _ = oracle.merge(*oracle.count(s, d, t, 2))
@@ -110,5 +122,5 @@ def test_mutant_is_caught(name, tmp_path):
     cfile = tmp_path / "m.c"
     cfile.write_text(mutated)
     so = tmp_path / "libm.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(cfile)])
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", str(so), str(cfile)])
     assert _with_lib(str(so)) != [], f"planted mistake {name} passed every pin"
