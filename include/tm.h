@@ -104,7 +104,8 @@ int tm_count_raw(const tm_graph *g, int64_t delta, uint64_t star[24], uint64_t p
  * Like tm_count, tm_count_raw and tm_count_select, it borrows about 36 bytes
  * per edge of scratch (window starts, the list of entries with Star/Pair
  * terms, the Tri joins) from the device's stream-ordered memory pool for the
- * duration of the count; tm_count_batch and tm_count_noalloc borrow none.
+ * duration of the count; the batched calls use a slab of their own and
+ * tm_count_noalloc uses none.
  */
 int tm_count_async(const tm_graph *g, int64_t delta, void *stream, uint64_t *dev_cells);
 
@@ -119,6 +120,21 @@ int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, i
                      uint64_t cells[56]);
 
 /*
+ * One shard of the centres (Sec. IV-C: centres are independent, so the
+ * counters are sums over centres): the Star and Pair cells and the Tri
+ * type-II cells of the centres u with owner[u] == rank, counted by the same
+ * kernels as tm_count (its window starts, Star/Pair list and Tri join, each
+ * join counting only the triangles centred at an owned endpoint). owner:
+ * int32[n] (n = tm_graph_nodes), host or device memory, read during the call.
+ * Tri types I and III are left zero: summing the cells of every rank (e.g. one
+ * all-reduce of the 56 cells over the ranks of a multi-GPU job, each with the
+ * whole graph built) and then tm_fill_tri_types gives tm_count_raw's cells.
+ * cells: host uint64[56]. Borrows pool scratch like tm_count plus 4 n bytes.
+ */
+int tm_count_shard(const tm_graph *g, int64_t delta, const int32_t *owner, int32_t rank,
+                   uint64_t cells[56]);
+
+/*
  * Category-selective counting (the per-category variants FAST-Pair /
  * FAST-Tri that the paper times separately, Sec. V-C, Table 3): what =
  * TM_SELECT_STAR_PAIR runs only Algorithm 1's counters (Star and Pair
@@ -130,8 +146,8 @@ int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, i
 int tm_count_select(const tm_graph *g, int64_t delta, int32_t what, uint64_t cells[56]);
 
 /*
- * Counts one graph for k windows deltas[0..k) in one batched launch (all k
- * counts share the persistent queue); out[i*36 .. i*36+36) as in tm_count.
+ * Counts one graph for k windows deltas[0..k) in one batched count (one
+ * segment per window); out[i*36 .. i*36+36) as in tm_count.
  * The paper's delta sensitivity experiment (Sec. V-E, Fig. 11(a)) is this
  * call over a list of deltas.
  */
@@ -145,22 +161,36 @@ int tm_count_multi(const tm_graph *g, const int64_t *deltas, int32_t k, uint64_t
  */
 int tm_merge(const uint64_t cells[56], uint64_t out[36]);
 
+/*
+ * Fills the Tri type-I and type-III cells of a 56-cell vector (host memory)
+ * from its type-II cells: each triangle instance adds one to a type-I, a
+ * type-II and a type-III cell of its class (Sec. IV-B counts every instance
+ * once per vertex), which gives Tri[II,i,j,k] = Tri[I,!k,!j,!i] =
+ * Tri[III,!i,k,j]. Used after summing type-II cells over shards of centres
+ * (tm_count_centres, tm_count_shard). Star and Pair cells are not touched.
+ * Returns TM_OK, or TM_EINVAL for NULL.
+ */
+int tm_fill_tri_types(uint64_t cells[56]);
+
 /* Writes the edge pattern of each class, codes[i*6+j] = pattern of
  * M_(i+1)(j+1): edges in time order, nodes 1,2,3 by first appearance, e.g.
  * "12 13 21". Returns TM_OK. */
 int tm_layout(char codes[36][16]);
 
 /*
- * Batched counting. Many graphs, each with its own window, are counted by
- * ONE persistent kernel launch fed by a device work queue: each graph's
- * incident entries are cut into work items (ranges of at most
- * item_entries entries, for the Star/Pair sweep and for the Tri join), the
- * items are queued largest first, and every block of the launch takes the
- * next item with one atomic until the queue is empty (the paper's dynamic
- * scheduling over centres, Sec. IV-C, as a device queue). The launch
- * sequence (job table and queue uploads, clears, the kernel, the Tri type
- * fill, the cell download) is captured once in a CUDA graph and replayed;
- * only the staged job table and queue change between calls. Synchronous.
+ * Batched counting. Many graphs, each with its own window, are counted
+ * together by the same kernels as one graph (window starts, Star/Pair sweep,
+ * Tri join), each kernel ONE persistent launch over a table of segments (a
+ * segment = one graph, or one component of a tm_build_many graph, or one
+ * window of tm_count_multi): its warps or blocks take units of work (entry
+ * ranges, listed entries, joins) of one segment at a time from the table in
+ * order, the paper's dynamic scheduling over centres (Sec. IV-C) as device
+ * work units. The launch sequence (segment table upload, clears, the kernels,
+ * the Tri type fill, the cell download) is captured once in a CUDA graph and
+ * replayed; only the staged table changes between calls. The scratch of the
+ * kernels (18 bytes per incident entry) is a device slab that the call keeps
+ * for the next batch and grows (cudaMalloc) only for a batch larger than all
+ * before it. Synchronous.
  */
 
 /* Counts gs[i] with window deltas[i] for i < n; out[i*36 .. i*36+36) as in
@@ -184,15 +214,16 @@ int32_t tm_graph_components(const tm_graph *g);
  * batched launch; out[c*36 .. c*36+36) as in tm_count. */
 int tm_count_many(const tm_graph *g, const int64_t *deltas, uint64_t *out);
 
-/* Batching parameters: entries per work item (>= 256; 0 keeps the current
- * value) and blocks per SM of the persistent launch (0 = as many as fit). */
+/* Batching parameters: entries per warp unit of the streaming passes
+ * (rounded down to a multiple of 128, at least 256; 0 keeps the current value)
+ * and blocks per SM of the Tri join (0 = as many as fit). */
 int tm_batch_config(int64_t item_entries, int32_t blocks_per_sm);
 int tm_batch_get_config(int64_t *item_entries, int32_t *blocks_per_sm);
 
 /* Autotuner: times tm_count_many on g with windows deltas (reps timed runs
- * per setting) over item sizes {4096, 16384, 65536, 262144} and blocks per
- * SM {1, 2, 4, ..., max}, checks that every setting gives the same cells,
- * makes the fastest the library's setting and reports it. */
+ * per setting) over units of {256, 512, 1024, 2048} entries and Tri-join
+ * blocks per SM {1, ..., max}, checks that every setting gives the same
+ * cells, makes the fastest the library's setting and reports it. */
 int tm_tune_batch(const tm_graph *g, const int64_t *deltas, int32_t reps,
                   int64_t *best_item_entries, int32_t *best_blocks_per_sm, double *best_ms);
 
@@ -225,9 +256,13 @@ typedef struct {
     double p50_ms, p99_ms, max_ms; /* latency quantiles of completed requests */
 } tm_server_stats_t;
 
-/* budget_bytes: device bytes for resident graphs plus builds in progress;
- * workers: 1..64 worker threads (streams); max_wave: most requests per wave.
- * NULL on error. */
+/* budget_bytes: device bytes for resident graphs, builds in progress and the
+ * workers' counting scratch (each worker counts its waves in runs of at most
+ * budget / (192 * workers) entries, 2^14..2^24, with a slab of 18 bytes per
+ * entry that it keeps; a larger graph is counted alone and charges the
+ * excess while resident); workers: 1..64 worker threads (streams);
+ * max_wave: most requests per wave. NULL on error (TM_EBUDGET when the
+ * workers' slabs alone exceed the budget). */
 tm_server *tm_server_create(int64_t budget_bytes, int32_t workers, int32_t max_wave);
 /* Returns the request id (>= 0) or a negative TM_E* code. A request whose
  * key names a resident graph counts that graph (its edges, if given, are not
@@ -243,17 +278,55 @@ int tm_server_wait(tm_server *s, int64_t id, uint64_t out[36], double *latency_m
                    double timeout_s);
 int tm_server_stats(tm_server *s, tm_server_stats_t *st);
 /* The server's admission estimate for a graph of m edges and n nodes: the
- * device bytes it holds while resident and the extra bytes its build needs
- * at peak (a new graph is admitted when both fit in the budget). */
+ * device bytes it holds while resident, and the extra bytes its build and a
+ * count of it alone need at peak (a new graph is admitted when they fit in
+ * the budget beside the workers' counting scratch, which the server reserves
+ * at creation: about 1/8 of the budget, at most 16M entries per worker). */
 int tm_estimate_bytes(int64_t m, int64_t n, int64_t *resident, int64_t *build_scratch);
 /* Keys of the resident graphs (up to cap written); returns how many there are. */
 int32_t tm_server_resident(tm_server *s, int64_t *keys, int32_t cap);
 /* Finishes the queued requests, stops the workers, frees every graph. */
 void tm_server_destroy(tm_server *s);
 
+/*
+ * Incremental counting of an edge stream. The paper motivates exact counts
+ * for frequently updated dynamic systems (Sec. I); a stream keeps the counts
+ * of every edge appended so far for one window delta without rebuilding the
+ * whole graph. tm_stream_append adds a batch of k edges (host or device
+ * arrays as in tm_build) whose timestamps are all >= the last timestamp
+ * appended before; edge ids continue from the edges before the batch, so a
+ * batch edge is ordered after every earlier edge of equal timestamp, and
+ * inside the batch by its index. The batch adds exactly the motif instances
+ * whose last edge is in it: every instance lies within delta of its last
+ * edge (Def. 2), so they are counted as cells(tail + batch) - cells(tail),
+ * where the tail is the appended edges within delta of the last timestamp
+ * (the only edges the stream keeps on the device; each of the two graphs is
+ * built and counted by the library's kernels). added (host uint64[56], may be
+ * NULL) receives the batch's raw cells; the running cells and classes come
+ * from tm_stream_counts. A failed append (TM_EINVAL: a timestamp below the
+ * last one, bad ids, tail + batch >= 2^30 edges) leaves the stream unchanged.
+ * Calls on one stream are serialised.
+ */
+typedef struct tm_stream tm_stream;
+tm_stream *tm_stream_create(int64_t delta);
+int tm_stream_append(tm_stream *st, const int32_t *src, const int32_t *dst, const int64_t *t,
+                     int64_t k, uint64_t added[56]);
+/* Running 56 raw cells and/or 36 classes (either may be NULL). */
+int tm_stream_counts(tm_stream *st, uint64_t cells[56], uint64_t out[36]);
+/* Edges appended so far / edges kept in the tail (-1 for NULL). */
+int64_t tm_stream_edges(tm_stream *st);
+int64_t tm_stream_tail(tm_stream *st);
+void tm_stream_free(tm_stream *st);
+
 /* Number of nodes / edges of a built graph (-1 for NULL). */
 int64_t tm_graph_nodes(const tm_graph *g);
 int64_t tm_graph_edges(const tm_graph *g);
+
+/* The compute capability the library's kernels were compiled for, as the
+ * CUDA runtime reports it for one of them on the current device
+ * (cudaFuncGetAttributes binaryVersion, e.g. 103 for sm_103a). Needs a CUDA
+ * device; returns TM_ECUDA without one. */
+int tm_kernel_arch(int32_t *arch);
 
 /* Kernels this library has launched in this process so far (all devices). */
 uint64_t tm_launch_count(void);

@@ -312,6 +312,32 @@ int tm_count_centres(const tm_graph *g, int64_t delta, const int32_t *centres, i
     });
 }
 
+int tm_count_shard(const tm_graph *g, int64_t delta, const int32_t *owner, int32_t rank,
+                   uint64_t cells[56]) {
+    return guarded([&] {
+        check_count_args(g, delta);
+        if (!owner || !cells || rank < 0) fail(TM_EINVAL, "bad shard arguments");
+        cudaStream_t s = lib_stream();
+        const int64_t n = g->g.n;
+        int32_t *own = dev_alloc_n<int32_t>(n, s);
+        unsigned long long *d = dev_alloc_n<unsigned long long>(NCELLS, s);
+        try {
+            if (n > 0)
+                TM_CUDA(cudaMemcpyAsync(own, owner, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+            TM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NCELLS, s));
+            launch_count_parts(g->g, delta, true, true, d, s, false, own, rank);
+            TM_CUDA(cudaMemcpyAsync(cells, d, sizeof(uint64_t) * NCELLS, cudaMemcpyDeviceToHost, s));
+            TM_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            dev_free(own, s);
+            dev_free(d, s);
+            throw;
+        }
+        dev_free(own, s);
+        dev_free(d, s);
+    });
+}
+
 int tm_count_select(const tm_graph *g, int64_t delta, int32_t what, uint64_t cells[56]) {
     return guarded([&] {
         check_count_args(g, delta);
@@ -342,6 +368,29 @@ int tm_merge(const uint64_t cells[56], uint64_t out[36]) {
         out[c] = v;
     }
     return bad;
+}
+
+int tm_fill_tri_types(uint64_t cells[56]) {
+    if (!cells) {
+        set_error(TM_EINVAL, "NULL cells");
+        return TM_EINVAL;
+    }
+    uint64_t *tri = cells + 32;
+    for (int di = 0; di < 2; di++)
+        for (int dj = 0; dj < 2; dj++)
+            for (int dk = 0; dk < 2; dk++) {
+                const uint64_t v = tri[8 + (di * 2 + dj) * 2 + dk];
+                tri[((1 - dk) * 2 + (1 - dj)) * 2 + (1 - di)] = v;     // type I
+                tri[16 + ((1 - di) * 2 + dk) * 2 + dj] = v;            // type III
+            }
+    return TM_OK;
+}
+
+int tm_kernel_arch(int32_t *arch) {
+    return guarded([&] {
+        if (!arch) fail(TM_EINVAL, "NULL arch");
+        *arch = kernel_binary_version();
+    });
 }
 
 int tm_layout(char codes[36][16]) {

@@ -1,9 +1,12 @@
 // Batched counting: many graphs (or the components of one multi-component
-// graph), each with its own delta, counted by one persistent launch fed by a
-// device work queue. The launch sequence (uploads of the job table and the
-// queue, clears, the persistent kernel, the type-I/III fill, the download of
-// the cells) is captured once in a CUDA graph and replayed; the queue is
-// data, so a new batch only rewrites the pinned staging buffers.
+// graph, or one graph for several windows), each with its own delta, counted
+// together as a table of segments by the fast count kernels: every kernel of
+// the sequence is one persistent launch over all segments, whose warps or
+// blocks take units of work (entry ranges, listed entries, joins) of one
+// segment at a time in order. The launch sequence (uploads of the segment
+// table, clears, the kernels, the type-I/III fill, the download of the cells)
+// is captured once in a CUDA graph and replayed; the table is data, so a new
+// batch only rewrites the pinned staging buffers.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -21,20 +24,26 @@ void free_graph(DevGraph &g, cudaStream_t s);
 
 namespace {
 
-// Process-wide batching parameters (set by tm_batch_config / tm_tune_batch).
-// Defaults: what tm_tune_batch picked on the 512-graph batch workload; small
-// items keep a window-heavy range from becoming the last block standing.
+// Process-wide batching parameters (set by tm_batch_config / tm_tune_batch):
+// entries per warp unit of the streaming passes and the Tri join's blocks
+// per SM (0: as many as fit).
 std::mutex g_cfg_mu;
-int64_t g_item_entries = 4096;
-int32_t g_blocks_per_sm = 2;  // 0: as many as fit
+int64_t g_item_entries = COUNT_ECHUNK;
+int32_t g_blocks_per_sm = 0;
 
 struct JobSpec {
     const DevGraph *g;
     int64_t delta;
-    int32_t tbegin, tend;  // the job's entries in g->T
+    int32_t tbegin, tend;  // the job's entries in g
 };
 
-// Reusable device + pinned buffers and the captured launch sequence.
+// Reusable device + pinned buffers and the captured launch sequence: the
+// segment table and its unit prefix are staged in pinned memory, and one
+// CUDA graph uploads them, clears the cells, runs the segmented count
+// (window starts, Star/Pair list, Tri jobs and join, type fill) and
+// downloads the cells. The scratch is one device block sized for the
+// plan's entry capacity, so a call allocates nothing unless the batch is
+// larger than every batch before it.
 class BatchPlan {
    public:
     ~BatchPlan() { release(); }
@@ -43,73 +52,67 @@ class BatchPlan {
     void run(const std::vector<JobSpec> &jobs, int64_t item_entries, int blocks_per_sm,
              cudaStream_t s, std::vector<uint64_t> &cells_out) {
         const int32_t nj = (int32_t)jobs.size();
-        items_.clear();
+        const int32_t echunk = (int32_t)std::max<int64_t>(128, item_entries / 128 * 128);
+        int64_t total = 0;
+        for (const JobSpec &j : jobs) total += (int64_t)j.tend - j.tbegin;
+        ensure(nj, total, blocks_per_sm, echunk, s);
+        int64_t xbase = 0;
+        h_meta_[0] = nj;
+        h_meta_[1] = 0;
         for (int32_t j = 0; j < nj; j++) {
+            Segment &sg = h_segs_[j];
+            sg.g = *jobs[j].g;
+            sg.delta = jobs[j].delta;
+            sg.cells = d_cells_ + (size_t)NCELLS * j;
+            sg.begin = jobs[j].tbegin;
+            sg.end = jobs[j].tend;
+            sg.xbase = xbase;
             const int64_t len = (int64_t)jobs[j].tend - jobs[j].tbegin;
-            for (int kind = 0; kind < 2; kind++)
-                for (int64_t b = jobs[j].tbegin; b < jobs[j].tend; b += item_entries) {
-                    const int64_t e = std::min<int64_t>(b + item_entries, jobs[j].tend);
-                    items_.push_back(WorkItem{j, kind, (int32_t)b, (int32_t)e});
-                }
-            (void)len;
+            xbase += len;
+            h_meta_[2 + j] = h_meta_[1 + j] + (int32_t)((len + echunk - 1) / echunk);
         }
-        // largest items first (the last items to finish are the short ones)
-        std::stable_sort(items_.begin(), items_.end(), [](const WorkItem &a, const WorkItem &b) {
-            return (a.end - a.begin) > (b.end - b.begin);
-        });
-        const int32_t ni = (int32_t)items_.size();
-        int sms = num_sms();
-        int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, batch_blocks_per_sm())
-                                    : batch_blocks_per_sm();
-        const int grid = std::max(1, sms * bps);
-        ensure(nj, ni, grid, s);
-        for (int32_t j = 0; j < nj; j++) {
-            h_jobs_[j].g = *jobs[j].g;
-            h_jobs_[j].delta = jobs[j].delta;
-            h_jobs_[j].cells = d_cells_ + (size_t)NCELLS * j;
-        }
-        if (ni) std::memcpy(h_items_, items_.data(), sizeof(WorkItem) * ni);
-        h_counts_[0] = ni;
-        h_counts_[1] = nj;
         TM_CUDA(cudaGraphLaunch(exec_, s));
-        g_launches.fetch_add(2, std::memory_order_relaxed);
+        g_launches.fetch_add(launches_per_run_, std::memory_order_relaxed);
         TM_CUDA(cudaStreamSynchronize(s));
         cells_out.assign(h_cells_, h_cells_ + (size_t)NCELLS * nj);
     }
 
    private:
-    void ensure(int32_t nj, int32_t ni, int grid, cudaStream_t s) {
-        if (exec_ && nj <= cap_jobs_ && ni <= cap_items_ && grid == grid_ && s == stream_) return;
+    void ensure(int32_t nj, int64_t entries, int bps, int32_t echunk, cudaStream_t s) {
+        if (exec_ && nj <= cap_jobs_ && entries <= cap_entries_ && bps == bps_ &&
+            echunk == echunk_ && s == stream_)
+            return;
+        const int32_t want_jobs = std::max(nj, cap_jobs_);
+        const int64_t want_entries = std::max(entries, cap_entries_);
         release();
         cap_jobs_ = 64;
-        while (cap_jobs_ < nj) cap_jobs_ <<= 1;
-        cap_items_ = 1024;
-        while (cap_items_ < ni) cap_items_ <<= 1;
-        grid_ = grid;
+        while (cap_jobs_ < want_jobs) cap_jobs_ <<= 1;
+        cap_entries_ = 1 << 16;
+        while (cap_entries_ < want_entries) cap_entries_ <<= 1;
+        bps_ = bps;
+        echunk_ = echunk;
         stream_ = s;
-        TM_CUDA(cudaMalloc(&d_jobs_, sizeof(BatchJob) * cap_jobs_));
-        TM_CUDA(cudaMalloc(&d_items_, sizeof(WorkItem) * cap_items_));
-        TM_CUDA(cudaMalloc(&d_counts_, sizeof(int32_t) * 4));
+        TM_CUDA(cudaMalloc(&d_segs_, sizeof(Segment) * cap_jobs_));
+        TM_CUDA(cudaMalloc(&d_meta_, sizeof(int32_t) * (cap_jobs_ + 2)));
         TM_CUDA(cudaMalloc(&d_cells_, sizeof(unsigned long long) * NCELLS * cap_jobs_));
-        TM_CUDA(cudaMallocHost(&h_jobs_, sizeof(BatchJob) * cap_jobs_));
-        TM_CUDA(cudaMallocHost(&h_items_, sizeof(WorkItem) * cap_items_));
-        TM_CUDA(cudaMallocHost(&h_counts_, sizeof(int32_t) * 4));
+        TM_CUDA(cudaMalloc(&d_scratch_, count_scratch_bytes(cap_entries_, cap_jobs_)));
+        TM_CUDA(cudaMallocHost(&h_segs_, sizeof(Segment) * cap_jobs_));
+        TM_CUDA(cudaMallocHost(&h_meta_, sizeof(int32_t) * (cap_jobs_ + 2)));
         TM_CUDA(cudaMallocHost(&h_cells_, sizeof(unsigned long long) * NCELLS * cap_jobs_));
-        std::memset(h_jobs_, 0, sizeof(BatchJob) * cap_jobs_);
-        std::memset(h_items_, 0, sizeof(WorkItem) * cap_items_);
+        std::memset(h_segs_, 0, sizeof(Segment) * cap_jobs_);
+        std::memset(h_meta_, 0, sizeof(int32_t) * (cap_jobs_ + 2));
+        count_scratch_carve(d_scratch_, cap_entries_, cap_jobs_, scratch_);
         cudaGraph_t graph;
+        const uint64_t l0 = g_launches.load();
         TM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         try {
-            TM_CUDA(cudaMemcpyAsync(d_jobs_, h_jobs_, sizeof(BatchJob) * cap_jobs_,
+            TM_CUDA(cudaMemcpyAsync(d_segs_, h_segs_, sizeof(Segment) * cap_jobs_,
                                     cudaMemcpyHostToDevice, s));
-            TM_CUDA(cudaMemcpyAsync(d_items_, h_items_, sizeof(WorkItem) * cap_items_,
+            TM_CUDA(cudaMemcpyAsync(d_meta_, h_meta_, sizeof(int32_t) * (cap_jobs_ + 2),
                                     cudaMemcpyHostToDevice, s));
-            TM_CUDA(cudaMemcpyAsync(d_counts_, h_counts_, sizeof(int32_t) * 2,
-                                    cudaMemcpyHostToDevice, s));
-            TM_CUDA(cudaMemsetAsync(d_counts_ + 2, 0, sizeof(int32_t), s));
             TM_CUDA(cudaMemsetAsync(d_cells_, 0, sizeof(unsigned long long) * NCELLS * cap_jobs_, s));
-            launch_batch(d_jobs_, d_items_, d_counts_, d_counts_ + 2, grid, s);
-            launch_fill_tri_types_batch(d_cells_, d_counts_ + 1, cap_jobs_, s);
+            launch_count_segments(nullptr, d_segs_, d_meta_, cap_jobs_, true, true, true, scratch_,
+                                  s, bps_, echunk_);
             TM_CUDA(cudaMemcpyAsync(h_cells_, d_cells_, sizeof(unsigned long long) * NCELLS * cap_jobs_,
                                     cudaMemcpyDeviceToHost, s));
         } catch (...) {
@@ -119,6 +122,9 @@ class BatchPlan {
             throw;
         }
         TM_CUDA(cudaStreamEndCapture(s, &graph));
+        // the captured launches were counted once; every replay counts them again
+        launches_per_run_ = g_launches.load() - l0;
+        g_launches.fetch_sub(launches_per_run_);
         cudaError_t e = cudaGraphInstantiate(&exec_, graph, 0);
         cudaGraphDestroy(graph);
         TM_CUDA(e);
@@ -127,34 +133,36 @@ class BatchPlan {
     void release() {
         if (exec_) cudaGraphExecDestroy(exec_);
         exec_ = nullptr;
-        cudaFree(d_jobs_);
-        cudaFree(d_items_);
-        cudaFree(d_counts_);
+        cudaFree(d_segs_);
+        cudaFree(d_meta_);
         cudaFree(d_cells_);
-        cudaFreeHost(h_jobs_);
-        cudaFreeHost(h_items_);
-        cudaFreeHost(h_counts_);
+        cudaFree(d_scratch_);
+        cudaFreeHost(h_segs_);
+        cudaFreeHost(h_meta_);
         cudaFreeHost(h_cells_);
-        d_jobs_ = nullptr;
-        d_items_ = nullptr;
-        d_counts_ = nullptr;
+        d_segs_ = nullptr;
+        d_meta_ = nullptr;
         d_cells_ = nullptr;
-        h_jobs_ = nullptr;
-        h_items_ = nullptr;
-        h_counts_ = nullptr;
+        d_scratch_ = nullptr;
+        h_segs_ = nullptr;
+        h_meta_ = nullptr;
         h_cells_ = nullptr;
-        cap_jobs_ = cap_items_ = 0;
+        cap_jobs_ = 0;
+        cap_entries_ = 0;
     }
 
-    std::vector<WorkItem> items_;
-    int32_t cap_jobs_ = 0, cap_items_ = 0;
-    int grid_ = 0;
+    int32_t cap_jobs_ = 0;
+    int64_t cap_entries_ = 0;
+    int bps_ = -1;
+    int32_t echunk_ = 0;
+    uint64_t launches_per_run_ = 0;
     cudaStream_t stream_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
-    BatchJob *d_jobs_ = nullptr, *h_jobs_ = nullptr;
-    WorkItem *d_items_ = nullptr, *h_items_ = nullptr;
-    int32_t *d_counts_ = nullptr, *h_counts_ = nullptr;  // nitems, njobs, head
+    Segment *d_segs_ = nullptr, *h_segs_ = nullptr;
+    int32_t *d_meta_ = nullptr, *h_meta_ = nullptr;  // k, unit prefix (k + 1)
     unsigned long long *d_cells_ = nullptr, *h_cells_ = nullptr;
+    void *d_scratch_ = nullptr;
+    CountScratch scratch_;
 };
 
 // One plan and one stream per device for the synchronous batched calls.
@@ -280,16 +288,31 @@ __global__ void k_comp_toff(const int32_t *__restrict__ off, const int32_t *__re
 void *new_batch_plan() { return new BatchPlan(); }
 void delete_batch_plan(void *plan) { delete static_cast<BatchPlan *>(plan); }
 
-// Counts whole graphs with their windows on stream s with a caller-owned plan.
+// Counts whole graphs with their windows on stream s with a caller-owned
+// plan, in runs of at most max_entries entries (a larger graph runs alone).
 void run_batch_on(const std::vector<const DevGraph *> &graphs, const std::vector<int64_t> &deltas,
-                  void *plan, cudaStream_t s, std::vector<uint64_t> &cells) {
-    std::vector<JobSpec> jobs;
-    for (size_t i = 0; i < graphs.size(); i++)
-        jobs.push_back(JobSpec{graphs[i], deltas[i], 0, (int32_t)(2 * graphs[i]->m)});
+                  void *plan, cudaStream_t s, int64_t max_entries, std::vector<uint64_t> &cells) {
     int64_t ie;
     int32_t bps;
     current_config(ie, bps);
-    static_cast<BatchPlan *>(plan)->run(jobs, ie, bps, s, cells);
+    cells.clear();
+    std::vector<JobSpec> run;
+    std::vector<uint64_t> part;
+    int64_t total = 0;
+    auto flush = [&] {
+        if (run.empty()) return;
+        static_cast<BatchPlan *>(plan)->run(run, ie, bps, s, part);
+        cells.insert(cells.end(), part.begin(), part.end());
+        run.clear();
+        total = 0;
+    };
+    for (size_t i = 0; i < graphs.size(); i++) {
+        const int64_t len = 2 * graphs[i]->m;
+        if (!run.empty() && (total + len > max_entries || (int32_t)run.size() >= 64)) flush();
+        run.push_back(JobSpec{graphs[i], deltas[i], 0, (int32_t)len});
+        total += len;
+    }
+    flush();
 }
 
 }  // namespace tmi
@@ -476,11 +499,10 @@ int tm_tune_batch(const tm_graph *g, const int64_t *deltas, int32_t reps, int64_
         check_graph(g);
         if (!deltas || reps <= 0) fail(TM_EINVAL, "bad tuning arguments");
         std::vector<JobSpec> jobs = component_jobs(g, deltas);
-        const int64_t ies[] = {4096, 16384, 65536, 262144};
-        const int maxb = batch_blocks_per_sm();
+        const int64_t ies[] = {256, 512, 1024, 2048};
+        const int maxb = count_join_blocks_per_sm();
         std::vector<int32_t> bpss;
-        for (int b = 1; b <= maxb; b *= 2) bpss.push_back(b);
-        if (bpss.back() != maxb) bpss.push_back(maxb);
+        for (int b = 1; b <= maxb; b++) bpss.push_back(b);
         double best = 1e300;
         int64_t bi = g_item_entries;
         int32_t bb = g_blocks_per_sm;

@@ -48,6 +48,10 @@
 // So k_window_lo lists the back-active entries while it finds every lo(r),
 // and k_star_pair_list makes each of them produce its own W terms and its
 // predecessor's F term; k_star_pair does the same per entry without scratch.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
 #include "tm_internal.cuh"
 
 namespace tmi {
@@ -55,6 +59,7 @@ namespace tmi {
 namespace {
 
 constexpr int THREADS = 256;
+constexpr int WARPS_PER_BLOCK = THREADS / 32;
 
 __device__ __forceinline__ int dir_of(uint32_t nbr) { return (int)(nbr >> 31); }
 
@@ -409,98 +414,274 @@ __device__ __forceinline__ int32_t gallop_fwd(const int64_t *__restrict__ tt, in
     return hi;
 }
 
-// lo(r) for every entry r in [begin, end): the first entry of W(r), r itself
-// when the window is empty. Each warp takes WLO_GROUPS consecutive groups of
-// 32 entries; a lane's entry in group g is 32 entries after its entry in
-// group g-1, and lo never decreases along one centre, so when both are of the
-// same centre the lane searches forwards from its previous lo (the window has
-// slid by about 32 entries) instead of backwards from r.
-// With `act`, the back-active entries (lk.x >= lo(r): a few percent, and the
-// only ones with Star/Pair contributions) are listed there as well, each warp
-// gathering them in shared memory and reserving space 32 at a time. The
-// order of the list is immaterial: every entry adds its counts.
-constexpr int WLO_GROUPS = 16;
+// ------------------------------------------------------------ segments
+//
+// The four kernels of the fast path (k_window_lo, k_star_pair_list,
+// k_tri_jobs, k_tri_join) count a table of segments in one pass each: a
+// segment is an entry range of one graph (whole edges: both entries of each
+// of its edges lie inside), its window delta and its 56 cells. One graph is
+// one segment; the components of a tm_build_many graph, the graphs of a batch
+// and the windows of a multi-delta call are one segment each. Scratch arrays
+// are indexed by x = the segment's xbase + (entry - its begin), so every
+// segment owns the scratch ranges [xbase, xbase + len) (window starts, the
+// list of back-active entries) and [xbase / 2, (xbase + len) / 2) (the Tri
+// joins, at most one per edge).
+//
+// Work is cut into units that never straddle two segments, taken by
+// persistent warps (or blocks) in index order: echunk consecutive entries for
+// the streaming passes, SP_CHUNK listed entries for the Star/Pair sweep, 32
+// joins for the Tri join.
+constexpr int SP_CHUNK = THREADS * 4;  // listed entries per block unit of the Star/Pair sweep
 
+struct SegArgs {
+    Segment seg0;          // the segment when segs is null
+    const Segment *segs;   // device table of the segments, or null: one segment, seg0
+    const int32_t *eunit;  // device, with segs: k, then the prefix over the segments of
+                           // ceil(len / echunk) (k + 1 values)
+    int32_t echunk;        // entries per warp unit of the streaming passes (a multiple of 128)
+    const int32_t *own;    // per node, the shard that owns it as a centre, or null: all
+    int32_t own_rank;      // the shard counted (centres u with own[u] == own_rank)
+};
+
+__device__ __forceinline__ bool owns(const SegArgs &A, uint32_t u) {
+    return A.own == nullptr || A.own[u] == A.own_rank;
+}
+
+// ONE: the kernel counts the single segment A.seg0 (read in place from the
+// kernel's parameter space); otherwise the device table A.segs.
+template <bool ONE>
+__device__ __forceinline__ int32_t seg_count(const SegArgs &A) {
+    return ONE ? 1 : A.eunit[0];
+}
+
+template <bool ONE>
+__device__ __forceinline__ const Segment &seg_ref(const SegArgs &A, int32_t c) {
+    if constexpr (ONE) return A.seg0;
+    else return A.segs[c];
+}
+
+// Largest c in [0, k) with pre[c] <= u (pre ascending, pre[0] = 0).
+__device__ __forceinline__ int32_t prefix_find(const int32_t *pre, int32_t k, int64_t u) {
+    int32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Number of streaming units over all segments, and the segment and first
+// entry of unit u.
+template <bool ONE>
+__device__ __forceinline__ int64_t seg_units(const SegArgs &A) {
+    if constexpr (ONE) return ((int64_t)A.seg0.end - A.seg0.begin + A.echunk - 1) / A.echunk;
+    else return A.eunit[1 + A.eunit[0]];
+}
+
+template <bool ONE>
+__device__ __forceinline__ int32_t unit_seg(const SegArgs &A, int64_t u, int64_t *first) {
+    if constexpr (ONE) {
+        *first = u;
+        return 0;
+    } else {
+        const int32_t c = prefix_find(A.eunit + 1, A.eunit[0], u);
+        *first = u - A.eunit[1 + c];
+        return c;
+    }
+}
+
+// A warp's buffered list entries (cnt of them, < 64) are appended to the
+// segment's list at list + xbase, 32 at a time or all at once (flush_all).
+__device__ __forceinline__ void warp_append(int32_t *buf, int &cnt, bool flush_all,
+                                            int32_t *__restrict__ list,
+                                            int32_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    while (cnt >= 32 || (flush_all && cnt > 0)) {
+        const int take = cnt >= 32 ? 32 : cnt;
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(count, take);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (lane < take) list[first + lane] = buf[cnt - take + lane];
+        cnt -= take;
+        __syncwarp();
+    }
+}
+
+// lo(r) for every entry r of every segment: the first entry of W(r), r
+// itself when the window is empty, written to wl[x(r)]. A warp takes a unit
+// of echunk consecutive entries of one segment as groups of 32; a lane's
+// entry in group g is 32 entries after its entry in group g-1, and lo never
+// decreases along one centre, so when both are of the same centre the lane
+// searches forwards from its previous lo (the window has slid by about 32
+// entries) instead of backwards from r.
+// With `act`, the back-active entries (lk.x >= lo(r): a few percent, and the
+// only ones with Star/Pair contributions) are listed there as well, in the
+// segment's own range act[xbase ...) with its count nact[c]; each warp
+// gathers them in shared memory and reserves space 32 at a time. The order
+// of a list is immaterial: every entry adds its counts.
+template <bool ONE>
 __global__ void __launch_bounds__(THREADS)
-    k_window_lo(const DevGraph g, int64_t delta, int32_t begin, int32_t end,
-                int32_t *__restrict__ wlo, int32_t *__restrict__ act,
-                int32_t *__restrict__ nact) {
+    k_window_lo(const __grid_constant__ SegArgs A, int32_t *__restrict__ wl,
+                int32_t *__restrict__ act, int32_t *__restrict__ nact) {
     __shared__ int32_t buf[THREADS / 32][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *wb = buf[warp];
-    int cnt = 0;  // entries held in wb (warp-uniform, < 32 between groups)
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr int64_t CHUNK = 32 * WLO_GROUPS;
-    for (int64_t c0 = begin + wid * CHUNK; c0 < end; c0 += nwarps * CHUNK) {
+    const int64_t nu = seg_units<ONE>(A);
+    for (int64_t u = wid; u < nu; u += nwarps) {
+        int64_t ui;
+        const int32_t c = unit_seg<ONE>(A, u, &ui);
+        const Segment &sg = seg_ref<ONE>(A, c);
+        const DevGraph &g = sg.g;
+        const int64_t delta = sg.delta;
+        const int64_t c0 = sg.begin + ui * A.echunk;
+        const int64_t end = c0 + A.echunk < sg.end ? c0 + A.echunk : sg.end;
+        int cnt = 0;  // entries held in wb (warp-uniform, < 32 between groups)
         int32_t prev_u = -1, prev_lo = 0;
-        for (int gi = 0; gi < WLO_GROUPS; gi++) {
+        for (int gi = 0; gi < A.echunk / 32; gi++) {
             const int64_t i = c0 + gi * 32 + lane;
             bool active = false;
             if (i < end) {
                 const int32_t r = (int32_t)i;
                 const int64_t tr = g.tt[r];
-                const int32_t u = g.tc[r];
+                const int32_t cu = g.tc[r];
                 int32_t lo = r;
-                if (u == prev_u) {
+                if (cu == prev_u) {
                     lo = gallop_fwd(g.tt, prev_lo, r, tr - delta, 32);
                 } else {
-                    const int32_t sb = g.off[u];
+                    const int32_t sb = g.off[cu];
                     if (r > sb && tr - g.tt[r - 1] <= delta) lo = gallop_lo(g.tt, sb, r, tr - delta);
                 }
-                prev_u = u;
+                prev_u = cu;
                 prev_lo = lo;
-                wlo[r] = lo;
-                active = act != nullptr && lo < r && g.lk[r].x >= lo;
+                wl[sg.xbase + (i - sg.begin)] = lo;
+                active = act != nullptr && lo < r && g.lk[r].x >= lo && owns(A, (uint32_t)cu);
             }
             if (act == nullptr) continue;
             const unsigned bal = __ballot_sync(0xffffffffu, active);
             if (active) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
             cnt += __popc(bal);
             __syncwarp();
-            if (cnt >= 32) {
-                int32_t first = 0;
-                if (lane == 0) first = atomicAdd(nact, 32);
-                first = __shfl_sync(0xffffffffu, first, 0);
-                act[first + lane] = wb[cnt - 32 + lane];
-                cnt -= 32;
-                __syncwarp();
-            }
+            warp_append(wb, cnt, false, act + sg.xbase, nact + c);
         }
-    }
-    if (act != nullptr && cnt > 0) {
-        int32_t first = 0;
-        if (lane == 0) first = atomicAdd(nact, cnt);
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (lane < cnt) act[first + lane] = wb[lane];
+        if (act != nullptr) warp_append(wb, cnt, true, act + sg.xbase, nact + c);
     }
 }
 
-// The Star/Pair sweep of the back-active entries that k_window_lo listed, 32
-// to a warp with every lane busy.
-__global__ void __launch_bounds__(THREADS, 5)
-    k_star_pair_list(const DevGraph g, int64_t delta, const int32_t *__restrict__ wlo,
-                     const int32_t *__restrict__ act, const int32_t *__restrict__ nact_ptr,
-                     unsigned long long *__restrict__ cells) {
-    // one copy of the 32 cells per lane index (shared by the block's warps),
-    // so the lanes of a warp never add to the same word
-    __shared__ unsigned long long sacc[32 * SP_COPIES];
-    for (int i = threadIdx.x; i < 32 * SP_COPIES; i += blockDim.x) sacc[i] = 0;
+// Prefix over the k segments of ceil(count[c] / chunk): out[0..k], one block.
+__global__ void k_unit_prefix(const int32_t *__restrict__ meta, const int32_t *__restrict__ count,
+                              int32_t chunk, int32_t *__restrict__ out) {
+    __shared__ int32_t carry;
+    const int32_t k = meta[0];
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    const int32_t nact = *nact_ptr;
-    unsigned long long *mine = sacc + (threadIdx.x & 31);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nact;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = act[i];
-        star_pair_back_active(g, delta, r, g.lk[r], wlo[r], mine);
+    for (int32_t b = 0; b < k; b += blockDim.x) {
+        const int32_t c = b + threadIdx.x;
+        const int32_t v = c < k ? (count[c] + chunk - 1) / chunk : 0;
+        int32_t inc = warp_incl_scan_i32(v);
+        __shared__ int32_t wsum[32];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const int32_t x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            const int32_t xi = warp_incl_scan_i32(x);
+            wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        inc += wsum[w];
+        if (c < k) out[c + 1] = carry + inc;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += inc;
+        __syncthreads();
     }
-    __syncthreads();
+    if (threadIdx.x == 0) out[0] = 0;
+}
+
+// Units of `chunk` listed items over the segments: with a table, from the
+// prefix pre (k_unit_prefix); for one segment, from its count.
+template <bool ONE>
+__device__ __forceinline__ int64_t list_units(const SegArgs &A, const int32_t *pre,
+                                              const int32_t *count, int32_t chunk) {
+    if constexpr (ONE) return (count[0] + chunk - 1) / chunk;
+    else return pre[A.eunit[0]];
+}
+
+template <bool ONE>
+__device__ __forceinline__ int32_t list_unit_seg(const SegArgs &A, const int32_t *pre, int64_t u,
+                                                 int64_t *first) {
+    if constexpr (ONE) {
+        *first = u;
+        return 0;
+    } else {
+        const int32_t c = prefix_find(pre, A.eunit[0], u);
+        *first = u - pre[c];
+        return c;
+    }
+}
+
+// The 32 Star/Pair cells of the block's copies (cell i of lane copy l at
+// sacc[i * SP_COPIES + l]) added into cells (Star 0..23, Pair 24..31).
+__device__ __forceinline__ void flush_lane_copies(const unsigned long long *sacc,
+                                                  unsigned long long *__restrict__ cells) {
     if (threadIdx.x < 32) {
         const int c = threadIdx.x;
         unsigned long long v = 0;
         for (int k = 0; k < 32; k++) v += sacc[c * SP_COPIES + k];
         if (v) atomicAdd(&cells[c < 8 ? 24 + c : c - 8], v);
     }
+}
+
+// The Star/Pair sweep of the back-active entries that k_window_lo listed, 32
+// to a warp with every lane busy. A block takes units of SP_CHUNK listed
+// entries of one segment and adds into its shared copies of the cells, which
+// it flushes into the segment's cells when the next unit belongs to another
+// segment, and at the end.
+template <bool ONE>
+__global__ void __launch_bounds__(THREADS, 5)
+    k_star_pair_list(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
+                     const int32_t *__restrict__ act, const int32_t *__restrict__ nact,
+                     const int32_t *__restrict__ sp_pre) {
+    // one copy of the 32 cells per lane index (shared by the block's warps),
+    // so the lanes of a warp never add to the same word
+    __shared__ unsigned long long sacc[32 * SP_COPIES];
+    for (int i = threadIdx.x; i < 32 * SP_COPIES; i += blockDim.x) sacc[i] = 0;
+    __syncthreads();
+    unsigned long long *mine = sacc + (threadIdx.x & 31);
+    const int64_t nu = list_units<ONE>(A, sp_pre, nact, SP_CHUNK);
+    int32_t cur = -1;
+    unsigned long long *cur_cells = nullptr;
+    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        int64_t ui;
+        const int32_t c = list_unit_seg<ONE>(A, sp_pre, u, &ui);  // block-uniform
+        const Segment &sg = seg_ref<ONE>(A, c);
+        if constexpr (!ONE) {
+            if (c != cur) {
+                if (cur >= 0) {
+                    __syncthreads();
+                    flush_lane_copies(sacc, cur_cells);
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < 32 * SP_COPIES; i += blockDim.x) sacc[i] = 0;
+                    __syncthreads();
+                }
+                cur = c;
+                cur_cells = sg.cells;
+            }
+        }
+        const int32_t n = nact[c];
+        for (int j = 0; j < SP_CHUNK / THREADS; j++) {
+            const int64_t idx = ui * SP_CHUNK + j * THREADS + threadIdx.x;
+            if (idx >= n) break;
+            const int32_t r = act[sg.xbase + idx];
+            star_pair_back_active(sg.g, sg.delta, r, sg.g.lk[r], wl[sg.xbase + (r - sg.begin)],
+                                  mine);
+        }
+    }
+    __syncthreads();
+    if constexpr (ONE) flush_lane_copies(sacc, A.seg0.cells);
+    else if (cur >= 0) flush_lane_copies(sacc, cur_cells);
 }
 
 // The Star/Pair sweep without scratch (window bounds searched per entry).
@@ -607,7 +788,8 @@ __device__ __forceinline__ bool pair_counts(const DevGraph &g, uint64_t key, int
 struct TriEdge {
     int32_t small_lo;     // smaller window: entries [small_lo, small_lo + work)
     int32_t work;
-    int32_t rank_lo_big;  // rank of the first entry of the bigger window
+    int32_t rank_lo_big;  // rank of the first entry of the bigger window; bit 30 / 31: do
+                          // not count the triangles centred at u / at w (a shard's join)
     uint32_t rj_s;        // rank of e_j; bit 31: the smaller window is W_u
     uint32_t big;         // the bigger window's centre
     __device__ __forceinline__ int32_t rank_j() const { return (int32_t)(rj_s & 0x7fffffffu); }
@@ -641,13 +823,29 @@ __device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, uint32_t big
                                                  unsigned long long (&acc)[8]) {
     const uint32_t x = node_of(it.x);
     PairCounts c;
-    if (!pair_counts_hashed(g, key, rank_lo_big, (int32_t)(rj_s & 0x7fffffffu), (int32_t)it.y, c))
+    if (!pair_counts_hashed(g, key, rank_lo_big & 0x3fffffff, (int32_t)(rj_s & 0x7fffffffu),
+                            (int32_t)it.y, c))
         return;
     // a big-side edge big -> x is outward at big and inward at x
     const bool big_is_min = big < x;
-    const int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
-    const int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
-    const int di = dir_of(it.x);                                // item w.r.t. its centre
+    int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
+    int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
+    const int di = dir_of(it.x);                          // item w.r.t. its centre
+    if (rank_lo_big & 0xc0000000) {
+        // a shard's join: the matches after the item are centred at the item's
+        // centre, those before it at the big window's centre
+        const bool skip_u = (rank_lo_big >> 30) & 1, skip_w = (uint32_t)rank_lo_big >> 31;
+        const bool skip_after = (rj_s >> 31) ? skip_u : skip_w;
+        const bool skip_before = (rj_s >> 31) ? skip_w : skip_u;
+        if (skip_after) {
+            c.na = 0;
+            a_out_big = 0;
+        }
+        if (skip_before) {
+            c.nb = 0;
+            b_out_big = 0;
+        }
+    }
     if (rj_s >> 31) {  // the smaller window is W_u
         // item a in W_u (node x), matches k in W_w.
         // after a: centre u, (e_i = a, e_k = k): Tri[II][d_a][0][dir of k w.r.t. x]
@@ -867,82 +1065,120 @@ __global__ void __launch_bounds__(THREADS)
     block_flush<8, 0>(acc, 32 + 8, cells);
 }
 
-// Whole-graph Tri in two steps, with the window starts wlo of k_window_lo.
-// k_tri_jobs: one thread per entry; every edge (at its source entry) whose
-// two windows are both non-empty becomes one join, appended to `jobs`. The
-// order of the jobs is immaterial: each adds its counts. Only a quarter of the
-// edges have such a join on the large workloads, so the joining warps below
-// get full lists instead of sparse ones, and the chain of dependent reads that
-// finds a join is paid here, in a kernel that does nothing else. A warp
-// gathers its jobs in shared memory and reserves space in `jobs` 32 at a time,
-// so the shared counter takes one atomic per 32 jobs.
+// Whole-graph Tri in two steps, with the window starts wl of k_window_lo.
+// k_tri_jobs: every edge (at its source entry) whose two windows are both
+// non-empty becomes one join, appended to its segment's range of `jobs`
+// (from xbase / 2, count njobs[c]). The order of the jobs is immaterial: each
+// adds its counts. Only a quarter of the edges have such a join on the large
+// workloads, so the joining warps below get full lists instead of sparse
+// ones, and the chain of dependent reads that finds a join is paid here, in
+// a kernel that does nothing else. A warp takes units of echunk entries of
+// one segment, gathers its jobs in shared memory and reserves space 32 at a
+// time, so the shared counter takes one atomic per 32 jobs.
+template <bool ONE>
 __global__ void __launch_bounds__(THREADS)
-    k_tri_jobs(const DevGraph g, const int32_t *__restrict__ wlo, TriEdge *__restrict__ jobs,
+    k_tri_jobs(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
+               TriEdge *__restrict__ jobs,
                int32_t *__restrict__ njobs) {
     constexpr int U = 4;  // groups of 32 entries per warp and step: U chains of reads in flight
     __shared__ TriEdge buf[TRI_WARPS][32 * (U + 1)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TriEdge *wb = buf[warp];
-    int cnt = 0;  // jobs held in wb (warp-uniform, < 32 between steps)
-    const int64_t n2 = 2 * g.m;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
-    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 * U);
-         base < n2; base += nwarps * 32 * U) {
-        uint2 en[U];
-        int32_t lo_u[U], twin[U], lo_w[U];
+    const int64_t nu = seg_units<ONE>(A);
+    for (int64_t u = wid; u < nu; u += nwarps) {
+        int64_t ui;
+        const int32_t c = unit_seg<ONE>(A, u, &ui);
+        const Segment &sg = seg_ref<ONE>(A, c);
+        const DevGraph &g = sg.g;
+        const int64_t c0 = sg.begin + ui * A.echunk;
+        const int64_t end = c0 + A.echunk < sg.end ? c0 + A.echunk : sg.end;
+        const int32_t *__restrict__ swl = wl + (sg.xbase - sg.begin);  // swl[r] = wl[x(r)]
+        TriEdge *sjobs = jobs + sg.xbase / 2;
+        int cnt = 0;  // jobs held in wb (warp-uniform, < 32 between steps)
+        for (int64_t base = c0; base < end; base += 32 * U) {
+            uint2 en[U];
+            int32_t lo_u[U], lo_w[U], twin[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-            const int64_t r = base + k * 32 + lane;
-            en[k] = make_uint2(0x80000000u, 0);  // inward: no join
-            lo_u[k] = 0;
-            if (r < n2) {
-                en[k] = g.tn[r];
-                lo_u[k] = wlo[r];
+            for (int k = 0; k < U; k++) {
+                const int64_t r = base + k * 32 + lane;
+                en[k] = make_uint2(0x80000000u, 0);  // inward: no join
+                lo_u[k] = 0;
+                if (r < end) {
+                    en[k] = g.tn[r];
+                    lo_u[k] = swl[r];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const int64_t r = base + k * 32 + lane;
+                twin[k] = -1;
+                if (dir_of(en[k].x) == 0 && lo_u[k] < r) twin[k] = g.pos_dst[en[k].y];
+            }
+#pragma unroll
+            for (int k = 0; k < U; k++) lo_w[k] = twin[k] >= 0 ? swl[twin[k]] : 0;
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const int64_t r = base + k * 32 + lane;
+                bool has = twin[k] >= 0 && lo_w[k] < twin[k];
+                TriEdge E;
+                if (has) {
+                    const uint32_t u = (uint32_t)g.tc[r], w = node_of(en[k].x);
+                    E = make_tri_edge(g, (int32_t)r, u, w, (int32_t)en[k].y, lo_u[k], twin[k],
+                                      lo_w[k]);
+                    if (A.own != nullptr) {
+                        const bool cu = owns(A, u), cw = owns(A, w);
+                        has = cu || cw;
+                        E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, has);
+                if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
+                cnt += __popc(bal);
+            }
+            __syncwarp();
+            while (cnt >= 32) {
+                int32_t first = 0;
+                if (lane == 0) first = atomicAdd(njobs + c, 32);
+                first = __shfl_sync(0xffffffffu, first, 0);
+                sjobs[first + lane] = wb[cnt - 32 + lane];
+                cnt -= 32;
+                __syncwarp();
             }
         }
-#pragma unroll
-        for (int k = 0; k < U; k++) {
-            const int64_t r = base + k * 32 + lane;
-            twin[k] = -1;
-            if (dir_of(en[k].x) == 0 && lo_u[k] < r) twin[k] = g.pos_dst[en[k].y];
-        }
-#pragma unroll
-        for (int k = 0; k < U; k++) lo_w[k] = twin[k] >= 0 ? wlo[twin[k]] : 0;
-#pragma unroll
-        for (int k = 0; k < U; k++) {
-            const int64_t r = base + k * 32 + lane;
-            const bool has = twin[k] >= 0 && lo_w[k] < twin[k];
-            TriEdge E;
-            if (has)
-                E = make_tri_edge(g, (int32_t)r, (uint32_t)g.tc[r], node_of(en[k].x),
-                                  (int32_t)en[k].y, lo_u[k], twin[k], lo_w[k]);
-            const unsigned bal = __ballot_sync(0xffffffffu, has);
-            if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
-            cnt += __popc(bal);
-        }
-        __syncwarp();
-        while (cnt >= 32) {
+        if (cnt > 0) {
             int32_t first = 0;
-            if (lane == 0) first = atomicAdd(njobs, 32);
+            if (lane == 0) first = atomicAdd(njobs + c, cnt);
             first = __shfl_sync(0xffffffffu, first, 0);
-            jobs[first + lane] = wb[cnt - 32 + lane];
-            cnt -= 32;
+            if (lane < cnt) sjobs[first + lane] = wb[lane];
             __syncwarp();
         }
     }
-    if (cnt > 0) {
-        int32_t first = 0;
-        if (lane == 0) first = atomicAdd(njobs, cnt);
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (lane < cnt) jobs[first + lane] = wb[lane];
+}
+
+// Adds each lane's 8 type-II counters of the warp into cells[40..47] (Tri
+// cells, T = II) and clears them.
+__device__ __forceinline__ void warp_flush_tri(unsigned long long (&acc)[8],
+                                               unsigned long long *__restrict__ cells) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        unsigned long long v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&cells[32 + 8 + c], v);
+        acc[c] = 0;
     }
 }
 
-// k_tri_join: each warp takes 32 consecutive jobs and runs their probes as
-// one flattened list, the hash lookups through the warp's queue.
+// k_tri_join: each warp takes units of 32 consecutive jobs of one segment
+// and runs their probes as one flattened list, the hash lookups through the
+// warp's queue. When its next unit belongs to another segment the warp
+// drains its queue and adds its counters into the segment's cells.
+template <bool ONE>
 __global__ void __launch_bounds__(THREADS, 5)
-    k_tri_join(const DevGraph g, const TriEdge *__restrict__ jobs,
-               const int32_t *__restrict__ njobs_ptr, unsigned long long *__restrict__ cells) {
+    k_tri_join(const __grid_constant__ SegArgs A, const TriEdge *__restrict__ jobs,
+               const int32_t *__restrict__ njobs, const int32_t *__restrict__ tj_pre) {
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
     __shared__ TriProbe queue[TRI_WARPS][TRI_QUEUE];
@@ -950,25 +1186,44 @@ __global__ void __launch_bounds__(THREADS, 5)
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t njobs = *njobs_ptr;
     const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
+    const int64_t nu = list_units<ONE>(A, tj_pre, njobs, 32);
     int qn = 0;
-    for (int64_t base = (blockIdx.x * (int64_t)TRI_WARPS + warp) * 32; base < njobs;
-         base += nwarps * 32) {
-        const int64_t j = base + lane;
+    int32_t cur = -1;
+    for (int64_t u = blockIdx.x * (int64_t)TRI_WARPS + warp; u < nu; u += nwarps) {
+        int64_t ui;
+        const int32_t c = list_unit_seg<ONE>(A, tj_pre, u, &ui);  // warp-uniform
+        if constexpr (!ONE) {
+            if (c != cur && cur >= 0) {
+                const Segment &prev = seg_ref<ONE>(A, cur);
+                tri_run_queue(prev.g, queue[warp], qn, acc);
+                qn = 0;
+                __syncwarp();
+                warp_flush_tri(acc, prev.cells);
+            }
+            cur = c;
+        }
+        const Segment &sg = seg_ref<ONE>(A, c);
+        const int64_t j = ui * 32 + lane;
         TriEdge E;
         E.work = 0;
-        if (j < njobs) E = jobs[j];
+        if (j < njobs[c]) E = jobs[sg.xbase / 2 + j];
         const int32_t inc = warp_incl_scan_i32(E.work);
         const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
         edges[warp][lane] = E;
         incl[warp][lane] = inc;
         __syncwarp();
-        tri_probes_queued(g, edges[warp], incl[warp], total, queue[warp], qn, acc);
+        tri_probes_queued(sg.g, edges[warp], incl[warp], total, queue[warp], qn, acc);
         __syncwarp();
     }
-    tri_run_queue(g, queue[warp], qn, acc);
-    block_flush<8, 0>(acc, 32 + 8, cells);
+    if constexpr (ONE) {
+        tri_run_queue(A.seg0.g, queue[warp], qn, acc);
+        block_flush<8, 0>(acc, 32 + 8, A.seg0.cells);
+    } else if (cur >= 0) {
+        const Segment &last = seg_ref<ONE>(A, cur);
+        tri_run_queue(last.g, queue[warp], qn, acc);
+        warp_flush_tri(acc, last.cells);
+    }
 }
 
 // Type II at the listed centres only: the entries of one centre, each as the
@@ -1028,50 +1283,12 @@ __global__ void k_fill_tri_types(unsigned long long *cells) {
             }
 }
 
-// The persistent batched count: every block repeatedly takes the next work
-// item (a range of one job's entries, largest items first) with one atomic
-// on the queue head, sweeps it with the same device functions as the
-// one-graph kernels, and adds its block total into that job's cells. The
-// queue is fixed for the launch, so no block ever waits for another.
-__global__ void __launch_bounds__(THREADS)
-    k_batch(const BatchJob *__restrict__ jobs, const WorkItem *__restrict__ items,
-            const int32_t *__restrict__ nitems_ptr, int32_t *__restrict__ head) {
-    __shared__ TriEdge edges[TRI_WARPS][32];
-    __shared__ int32_t incl[TRI_WARPS][32];
-    __shared__ int32_t cur;
-    __shared__ unsigned long long sacc[32];
-    const int32_t nitems = *nitems_ptr;
-    const int warp = threadIdx.x >> 5;
-    while (true) {
-        __syncthreads();  // the previous item's reads of `cur` are done
-        if (threadIdx.x == 0) cur = atomicAdd(head, 1);
-        __syncthreads();
-        const int32_t i = cur;
-        if (i >= nitems) break;
-        const WorkItem it = items[i];
-        const DevGraph g = jobs[it.job].g;
-        const int64_t delta = jobs[it.job].delta;
-        unsigned long long *cells = jobs[it.job].cells;
-        if (it.kind == 0) {
-            if (threadIdx.x < 32) sacc[threadIdx.x] = 0;
-            __syncthreads();
-            star_pair_range(g, delta, it.begin, it.end, threadIdx.x, blockDim.x, sacc);
-            __syncthreads();
-            flush_star_pair(sacc, cells);
-        } else {
-            unsigned long long acc[8];
-#pragma unroll
-            for (int c = 0; c < 8; c++) acc[c] = 0;
-            tri_range(g, delta, it.begin, it.end, warp, TRI_WARPS, edges[warp], incl[warp], acc);
-            block_flush<8, 0>(acc, 32 + 8, cells);
-        }
-    }
-}
-
-__global__ void k_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *njobs) return;
-    unsigned long long *tri = cells + (size_t)NCELLS * j + 32;
+// Type-I/III Tri cells of every segment from its type-II cells.
+template <bool ONE>
+__global__ void k_fill_tri_types_seg(const __grid_constant__ SegArgs A) {
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= seg_count<ONE>(A)) return;
+    unsigned long long *tri = seg_ref<ONE>(A, c).cells + 32;
     for (int di = 0; di < 2; di++)
         for (int dj = 0; dj < 2; dj++)
             for (int dk = 0; dk < 2; dk++) {
@@ -1083,20 +1300,105 @@ __global__ void k_fill_tri_types_batch(unsigned long long *cells, const int32_t 
 
 }  // namespace
 
-int batch_blocks_per_sm() {
+int kernel_binary_version() {
+    cudaFuncAttributes a;
+    TM_CUDA(cudaFuncGetAttributes(&a, k_fill_tri_types));
+    return a.binaryVersion;
+}
+
+namespace {
+
+template <typename K>
+int occupancy(K kernel) {
     int nb = 0;
-    TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, THREADS, 0));
+    TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, THREADS, 0));
     return nb > 0 ? nb : 1;
 }
 
-void launch_batch(const BatchJob *jobs, const WorkItem *items, const int32_t *nitems,
-                  int32_t *head, int grid, cudaStream_t s) {
-    TM_LAUNCH(k_batch, (unsigned)grid, THREADS, 0, s, jobs, items, nitems, head);
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t count_scratch_bytes(int64_t entries, int32_t k) {
+    const int64_t e = entries > 0 ? entries : 1;
+    return align_up(sizeof(int32_t) * e) + align_up(sizeof(int32_t) * e) +
+           align_up(sizeof(TriEdge) * (e / 2 + 1)) + align_up(sizeof(int32_t) * (4 * (size_t)k + 4));
 }
 
-void launch_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs, int max_jobs,
-                                 cudaStream_t s) {
-    TM_LAUNCH(k_fill_tri_types_batch, (unsigned)((max_jobs + 127) / 128), 128, 0, s, cells, njobs);
+void count_scratch_carve(void *base, int64_t entries, int32_t k, CountScratch &sc) {
+    const int64_t e = entries > 0 ? entries : 1;
+    char *p = static_cast<char *>(base);
+    sc.wl = reinterpret_cast<int32_t *>(p);
+    p += align_up(sizeof(int32_t) * e);
+    sc.act = reinterpret_cast<int32_t *>(p);
+    p += align_up(sizeof(int32_t) * e);
+    sc.jobs = p;
+    p += align_up(sizeof(TriEdge) * (e / 2 + 1));
+    sc.counts = reinterpret_cast<int32_t *>(p);  // nact[k] | njobs[k] | sp_pre[k+1] | tj_pre[k+1]
+    sc.k_cap = k;
+}
+
+int count_join_blocks_per_sm() { return occupancy(k_tri_join<false>); }
+
+void launch_count_segments(const Segment *one, const Segment *d_segs, const int32_t *d_meta,
+                           int32_t k_cap, bool star_pair, bool tri, bool fill,
+                           const CountScratch &sc, cudaStream_t s, int join_blocks_per_sm,
+                           int32_t echunk, const int32_t *own, int32_t own_rank) {
+    if (echunk < 128 || echunk % 128) fail(TM_EINVAL, "entries per unit must be a multiple of 128");
+    SegArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.echunk = echunk;
+    A.own = own;
+    A.own_rank = own_rank;
+    const int sms = num_sms();
+    // the streaming passes: one block per 8 units, at most 8 blocks per SM (a
+    // table's unit count is only known on the device: the cap)
+    int64_t stream_blocks = (int64_t)sms * 8;
+    if (one) {
+        A.seg0 = *one;
+        const int64_t units = ((int64_t)one->end - one->begin + echunk - 1) / echunk;
+        if (units == 0) return;
+        stream_blocks = std::min(stream_blocks, (units + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    } else {
+        A.segs = d_segs;
+        A.eunit = d_meta;
+    }
+    const int k = one ? 1 : k_cap;
+    int32_t *nact = sc.counts, *njobs = sc.counts + k, *sp_pre = sc.counts + 2 * k,
+            *tj_pre = sc.counts + 3 * k + 1;
+    TM_CUDA(cudaMemsetAsync(sc.counts, 0, sizeof(int32_t) * 2 * k, s));
+    {
+        PhaseTimer pt(TM_PH_STAR_PAIR, s);
+        int32_t *act = star_pair ? sc.act : nullptr;
+        if (one) TM_LAUNCH(k_window_lo<true>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
+        else TM_LAUNCH(k_window_lo<false>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
+        if (star_pair) {
+            const unsigned grid = (unsigned)(sms * occupancy(k_star_pair_list<true>));
+            if (one) {
+                TM_LAUNCH(k_star_pair_list<true>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre);
+            } else {
+                TM_LAUNCH(k_unit_prefix, 1, 1024, 0, s, d_meta, nact, SP_CHUNK, sp_pre);
+                TM_LAUNCH(k_star_pair_list<false>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre);
+            }
+        }
+    }
+    if (tri) {
+        PhaseTimer pt(TM_PH_TRI, s);
+        TriEdge *jobs = static_cast<TriEdge *>(sc.jobs);
+        const int occ = occupancy(k_tri_join<true>);
+        const int bps = join_blocks_per_sm > 0 ? std::min(join_blocks_per_sm, occ) : occ;
+        if (one) {
+            TM_LAUNCH(k_tri_jobs<true>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs, njobs);
+            TM_LAUNCH(k_tri_join<true>, (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs, tj_pre);
+            if (fill) TM_LAUNCH(k_fill_tri_types_seg<true>, 1, 128, 0, s, A);
+        } else {
+            TM_LAUNCH(k_tri_jobs<false>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs, njobs);
+            TM_LAUNCH(k_unit_prefix, 1, 1024, 0, s, d_meta, njobs, 32, tj_pre);
+            TM_LAUNCH(k_tri_join<false>, (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs, tj_pre);
+            if (fill)
+                TM_LAUNCH(k_fill_tri_types_seg<false>, (unsigned)((k + 127) / 128), 128, 0, s, A);
+        }
+    }
 }
 
 void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
@@ -1121,48 +1423,23 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
 }
 
 void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,
-                        unsigned long long *dev_cells, cudaStream_t s, bool fill) {
+                        unsigned long long *dev_cells, cudaStream_t s, bool fill,
+                        const int32_t *own, int32_t own_rank) {
     const int64_t n = 2 * g.m;
     if (n == 0) return;
-    int64_t blocks = (n + THREADS - 1) / THREADS;
-    const int64_t cap = (int64_t)num_sms() * 8;
-    if (blocks > cap) blocks = cap;
-    // the window start of every entry, found once for both sweeps
-    int32_t *wlo = dev_alloc_n<int32_t>(n, s);
-    {
-        PhaseTimer pt(TM_PH_STAR_PAIR, s);
-        int32_t *act = nullptr, *nact = nullptr;
-        if (star_pair) {
-            act = dev_alloc_n<int32_t>(n + 1, s);  // the list, then its length
-            nact = act + n;
-            TM_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
-        }
-        TM_LAUNCH(k_window_lo, (unsigned)blocks, THREADS, 0, s, g, delta, 0, (int32_t)n, wlo, act,
-                  nact);
-        if (star_pair) {
-            int per_sm = 0;
-            TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list,
-                                                                  THREADS, 0));
-            TM_LAUNCH(k_star_pair_list, (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1)), THREADS,
-                      0, s, g, delta, wlo, act, nact, dev_cells);
-            dev_free(act, s);
-        }
-    }
-    if (tri) {
-        PhaseTimer pt(TM_PH_TRI, s);
-        TriEdge *jobs = dev_alloc_n<TriEdge>(g.m, s);  // at most one join per edge
-        int32_t *njobs = dev_alloc_n<int32_t>(1, s);
-        TM_CUDA(cudaMemsetAsync(njobs, 0, sizeof(int32_t), s));
-        TM_LAUNCH(k_tri_jobs, (unsigned)blocks, THREADS, 0, s, g, wlo, jobs, njobs);
-        int per_sm = 0;
-        TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_join, THREADS, 0));
-        TM_LAUNCH(k_tri_join, (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1)), THREADS, 0, s, g,
-                  jobs, njobs, dev_cells);
-        if (fill) TM_LAUNCH(k_fill_tri_types, 1, 32, 0, s, dev_cells);
-        dev_free(jobs, s);
-        dev_free(njobs, s);
-    }
-    dev_free(wlo, s);
+    Segment one;
+    one.g = g;
+    one.delta = delta;
+    one.cells = dev_cells;
+    one.begin = 0;
+    one.end = (int32_t)n;
+    one.xbase = 0;
+    void *mem = dev_alloc(count_scratch_bytes(n, 1), s);
+    CountScratch sc;
+    count_scratch_carve(mem, n, 1, sc);
+    launch_count_segments(&one, nullptr, nullptr, 1, star_pair, tri, fill, sc, s, 0,
+                          COUNT_ECHUNK, own, own_rank);
+    dev_free(mem, s);
 }
 
 void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,

@@ -24,7 +24,7 @@ void build_graph(const int32_t *src, const int32_t *dst, const int64_t *t, int64
                  cudaStream_t s, DevGraph &g);
 void free_graph(DevGraph &g, cudaStream_t s);
 void run_batch_on(const std::vector<const DevGraph *> &graphs, const std::vector<int64_t> &deltas,
-                  void *plan, cudaStream_t s, std::vector<uint64_t> &cells);
+                  void *plan, cudaStream_t s, int64_t max_entries, std::vector<uint64_t> &cells);
 void *new_batch_plan();
 void delete_batch_plan(void *plan);
 
@@ -41,6 +41,23 @@ int64_t resident_bytes(int64_t m, int64_t n) {
     return 64 * m + 4 + 8 * m + 8 * (m + 1) + 16 * hash + 4 * (n + 1) + m + (1 << 20);
 }
 int64_t build_scratch_bytes(int64_t m) { return 96 * m + (1 << 20); }
+
+// Each worker counts its waves in runs of at most count_cap entries with a
+// scratch slab of count_scratch_bytes(count_cap, WAVE_JOBS) bytes that it
+// keeps; the server reserves the workers' slabs in its budget. A graph with
+// more entries than that is counted alone with a larger slab, and the excess
+// is charged to the graph while it is resident.
+constexpr int32_t WAVE_JOBS = 64;
+int64_t count_cap_entries(int64_t budget, int32_t workers) {
+    int64_t cap = budget / (8 * (int64_t)workers * 24);
+    if (cap > (int64_t(1) << 24)) cap = int64_t(1) << 24;
+    if (cap < (int64_t(1) << 14)) cap = int64_t(1) << 14;
+    return cap;
+}
+int64_t count_excess_bytes(int64_t m, int64_t cap) {
+    if (2 * m <= cap) return 0;
+    return (int64_t)count_scratch_bytes(2 * m, WAVE_JOBS) - (int64_t)count_scratch_bytes(cap, WAVE_JOBS);
+}
 
 struct Request {
     int64_t id;
@@ -81,6 +98,9 @@ struct tm_server {
     std::unordered_map<int64_t, tmi::Resident> cache;  // by graph key
     std::list<int64_t> lru;                            // front = least recently used
     int64_t used = 0;                                  // resident + reserved bytes
+    int64_t count_cap = 0;                             // entries per counting run
+    int64_t reserved = 0;                              // the workers' counting slabs
+    int32_t busy = 0;                                  // workers with a wave in flight
     int64_t next_id = 0;
     // statistics
     int64_t completed = 0, failed = 0, evictions = 0, builds = 0, waves = 0, edges_counted = 0;
@@ -174,8 +194,9 @@ void worker_loop(tm_server *S) {
                     continue;
                 }
                 const int64_t m = (int64_t)r->src.size();
-                const int64_t need = resident_bytes(m, r->n_hint) + build_scratch_bytes(m);
-                if (need > S->budget) {
+                const int64_t need = resident_bytes(m, r->n_hint) + build_scratch_bytes(m) +
+                                     count_excess_bytes(m, S->count_cap);
+                if (need > S->budget - S->reserved) {
                     finish(S, r, TM_EBUDGET, "graph does not fit in the server's memory budget");
                     it = S->pending.erase(it);
                     S->cv_done.notify_all();
@@ -196,11 +217,22 @@ void worker_loop(tm_server *S) {
                 it = S->pending.erase(it);
             }
             if (wave.empty()) {
+                if (S->busy == 0) {
+                    // no wave in flight and every idle graph evicted: what is still
+                    // pending can never be admitted
+                    for (Request *r : S->pending)
+                        finish(S, r, TM_EBUDGET,
+                               "graph does not fit beside the server's reserved scratch");
+                    S->pending.clear();
+                    S->cv_done.notify_all();
+                    continue;
+                }
                 // nothing admissible now: wait for a wave to finish or new work
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
             S->waves++;
+            S->busy++;
         }
         // build the new graphs of the wave on this worker's stream
         std::vector<int> ok(wave.size(), 1);
@@ -229,7 +261,8 @@ void worker_loop(tm_server *S) {
             res.g = g;
             res.building = false;
             // the build scratch is back in the pool: keep only the resident bytes
-            const int64_t keep = resident_bytes(g->g.m, g->g.n);
+            const int64_t keep =
+                resident_bytes(g->g.m, g->g.n) + count_excess_bytes(g->g.m, S->count_cap);
             S->used -= res.bytes - keep;
             res.bytes = keep;
             S->builds++;
@@ -251,7 +284,7 @@ void worker_loop(tm_server *S) {
         int status = TM_OK;
         std::string err;
         try {
-            if (!gs.empty()) run_batch_on(gs, deltas, plan, s, cells);
+            if (!gs.empty()) run_batch_on(gs, deltas, plan, s, S->count_cap, cells);
         } catch (const Error &e) {
             status = e.code;
             err = e.msg;
@@ -270,6 +303,7 @@ void worker_loop(tm_server *S) {
                 auto c = S->cache.find(we.r->key);
                 if (c != S->cache.end()) c->second.refs--;
             }
+            S->busy--;
         }
         S->cv_done.notify_all();
         S->cv_work.notify_all();
@@ -293,6 +327,15 @@ tm_server *tm_server_create(int64_t budget_bytes, int32_t workers, int32_t max_w
     tm_server *S = new tm_server();
     S->budget = budget_bytes;
     S->max_wave = max_wave;
+    S->count_cap = count_cap_entries(budget_bytes, workers);
+    // the workers' counting slabs are held for the server's lifetime
+    S->reserved = (int64_t)workers * (int64_t)count_scratch_bytes(S->count_cap, WAVE_JOBS);
+    S->used = S->reserved;
+    if (S->used >= budget_bytes) {
+        record_error(TM_EBUDGET, "tm_server_create: budget below the workers' counting scratch");
+        delete S;
+        return nullptr;
+    }
     try {
         S->device = current_device_id();
         num_sms();  // per-device set-up before the workers start
@@ -405,7 +448,8 @@ int tm_server_stats(tm_server *S, tm_server_stats_t *st) {
 int tm_estimate_bytes(int64_t m, int64_t n, int64_t *resident, int64_t *build_scratch) {
     if (m < 0 || n < 0) return TM_EINVAL;
     if (resident) *resident = resident_bytes(m, n);
-    if (build_scratch) *build_scratch = build_scratch_bytes(m);
+    if (build_scratch)
+        *build_scratch = build_scratch_bytes(m) + (int64_t)count_scratch_bytes(2 * m, 1);
     return TM_OK;
 }
 

@@ -199,42 +199,65 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
 void launch_fill_tri_types(unsigned long long *dev_cells, cudaStream_t s);
 
 // Only the Star/Pair kernel and/or only the Tri kernel (with its type fill
-// unless fill is false), after the window-start pass both of them read.
+// unless fill is false), after the window-start pass both of them read. With
+// `own` (device int32[n]), only the centres u with own[u] == own_rank are
+// counted (a shard of the centres; Tri type II only, fill must be false).
 void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,
-                        unsigned long long *dev_cells, cudaStream_t s, bool fill = true);
+                        unsigned long long *dev_cells, cudaStream_t s, bool fill = true,
+                        const int32_t *own = nullptr, int32_t own_rank = 0);
 
 // The whole-graph count (Star/Pair, Tri, type-I/III fill) into dev_cells with
 // no phase timers and no allocation of any kind.
 void launch_count_untimed(const DevGraph &g, int64_t delta, unsigned long long *dev_cells,
                           cudaStream_t s);
 
-// ---------------------------------------------------------- batching
+// ------------------------------------------------- segmented counting
 
-// One counting job of a batched launch: a graph (or one component of a
-// multi-component graph), its window and its 56 output cells.
-struct BatchJob {
+// One counting segment: the entries [begin, end) of graph g (whole edges:
+// both entries of each of its edges lie inside), counted with window delta
+// into the 56 device cells at `cells`. Its scratch is indexed from xbase (an
+// even number: the sum of the lengths of the segments before it).
+struct Segment {
     DevGraph g;
     int64_t delta;
     unsigned long long *cells;
+    int32_t begin, end;
+    int64_t xbase;
 };
 
-// A contiguous range of one job's incident entries, for the Star/Pair sweep
-// (kind 0) or the Tri join (kind 1).
-struct WorkItem {
-    int32_t job;
-    int32_t kind;
-    int32_t begin;
-    int32_t end;
+// Scratch of a segmented count: window starts (4 B per entry), lists of
+// back-active entries (4 B per entry), Tri joins (20 B per edge) and the
+// per-segment counters and unit prefixes, carved from one device block.
+struct CountScratch {
+    int32_t *wl = nullptr;
+    int32_t *act = nullptr;
+    void *jobs = nullptr;
+    int32_t *counts = nullptr;
+    int32_t k_cap = 0;
 };
+size_t count_scratch_bytes(int64_t entries, int32_t k);
+void count_scratch_carve(void *base, int64_t entries, int32_t k, CountScratch &sc);
 
-// One persistent launch: `grid` blocks pop items from `items[0, *nitems)` in
-// order through the counter *head, which must be zero at launch.
-void launch_batch(const BatchJob *jobs, const WorkItem *items, const int32_t *nitems,
-                  int32_t *head, int grid, cudaStream_t s);
-// Type-I/III Tri cells of jobs [0, *njobs) from their type-II cells.
-void launch_fill_tri_types_batch(unsigned long long *cells, const int32_t *njobs, int max_jobs,
-                                 cudaStream_t s);
-int batch_blocks_per_sm();
+// Entries per warp unit of the streaming count passes on the one-graph path.
+constexpr int32_t COUNT_ECHUNK = 512;
+
+// The fast count (window starts, Star/Pair list sweep, Tri jobs and join,
+// type-I/III fill) of one segment (`one`, host) or of a device table of
+// segments (d_segs; d_meta = {k, prefix over the segments of their units of
+// echunk entries, k + 1 values}; k_cap bounds k and sizes the counters).
+// Scratch must cover the total entries of the segments. join_blocks_per_sm
+// limits the Tri join's occupancy (0: as many as fit); echunk (a multiple of
+// 128) is the entries per warp unit of the streaming passes. With a table,
+// every launch reads its sizes from device memory, so the sequence can be
+// captured in a CUDA graph once and replayed for any table within the
+// capacities.
+void launch_count_segments(const Segment *one, const Segment *d_segs, const int32_t *d_meta,
+                           int32_t k_cap, bool star_pair, bool tri, bool fill,
+                           const CountScratch &sc, cudaStream_t s, int join_blocks_per_sm,
+                           int32_t echunk, const int32_t *own = nullptr, int32_t own_rank = 0);
+int count_join_blocks_per_sm();
+// binaryVersion of a library kernel on the current device (e.g. 103).
+int kernel_binary_version();
 
 // Read access to a built graph, and error recording, for entry points that
 // live outside api.cu.

@@ -4,7 +4,8 @@ Centres are independent (Sec. IV-C, inter-node parallelism): the Star/Pair
 counters and the Tri type-II counters of a graph are sums over centres. A
 rank that counts the centres of its shard (tm_count_centres) and an
 all-reduce of the 56 cells therefore give the whole graph's counters; the Tri
-type-I/III cells are filled from the summed type-II cells afterwards.
+type-I/III cells are filled from the summed type-II cells afterwards, by the
+library.
 
 This module only assigns centres and sums cells; it runs no counting.
 """
@@ -28,19 +29,14 @@ def all_reduce_cells(cells, dist=None):
         return cells
     import torch
     t = torch.from_numpy(cells.astype(np.int64))  # sums stay below 2^63 here
+    if dist.get_backend() == "nccl":
+        t = t.cuda()  # NCCL reduces device tensors
     dist.all_reduce(t)
-    return t.numpy().astype(np.uint64)
+    return t.cpu().numpy().astype(np.uint64)
 
 
-def fill_tri_types(tri):
-    """Type-I and type-III Tri cells from the type-II cells (each triangle
-    instance adds one to a cell of each type of its class, Sec. IV-B):
-    Tri[II,i,j,k] = Tri[I,!k,!j,!i] = Tri[III,!i,k,j]."""
-    tri = np.array(tri, np.uint64).reshape(3, 2, 2, 2)
-    for i in range(2):
-        for j in range(2):
-            for k in range(2):
-                v = tri[1, i, j, k]
-                tri[0, 1 - k, 1 - j, 1 - i] = v
-                tri[2, 1 - i, k, j] = v
-    return tri
+def fill_tri_types(cells):
+    """The summed 56 cells with the Tri type-I/III cells filled from type II,
+    by the library (tm_fill_tri_types)."""
+    from . import tm
+    return tm.fill_tri_types(cells)

@@ -36,6 +36,18 @@ _lib.tm_count_async.argtypes = [_P, _i64, _P, _P]
 _lib.tm_count_centres.argtypes = [_P, _i64, _P, ctypes.c_int32, _P]
 _lib.tm_merge.argtypes = [_P, _P]
 _lib.tm_layout.argtypes = [_P]
+_lib.tm_fill_tri_types.argtypes = [_P]
+_lib.tm_count_shard.argtypes = [_P, _i64, _P, ctypes.c_int32, _P]
+_lib.tm_stream_create.restype = _P
+_lib.tm_stream_create.argtypes = [_i64]
+_lib.tm_stream_append.argtypes = [_P, _P, _P, _P, _i64, _P]
+_lib.tm_stream_counts.argtypes = [_P, _P, _P]
+_lib.tm_stream_edges.restype = _i64
+_lib.tm_stream_edges.argtypes = [_P]
+_lib.tm_stream_tail.restype = _i64
+_lib.tm_stream_tail.argtypes = [_P]
+_lib.tm_stream_free.argtypes = [_P]
+_lib.tm_kernel_arch.argtypes = [_P]
 _lib.tm_graph_nodes.restype = _i64
 _lib.tm_graph_nodes.argtypes = [_P]
 _lib.tm_graph_edges.restype = _i64
@@ -415,6 +427,52 @@ class Server:
             pass
 
 
+class Stream:
+    """Incremental counting of an edge stream for one window (tm_stream_*):
+    append time-ordered batches; each returns the raw cells it added."""
+
+    def __init__(self, delta):
+        h = _lib.tm_stream_create(int(delta))
+        if not h:
+            code, msg = last_error()
+            raise TmError(code, msg)
+        self._h = h
+
+    def append(self, src, dst, t):
+        s, keep_s = _ptr(src, np.int32)
+        d, keep_d = _ptr(dst, np.int32)
+        tt, keep_t = _ptr(t, np.int64)
+        added = np.zeros(56, np.uint64)
+        _check(_lib.tm_stream_append(self._h, s, d, tt, len(src), added.ctypes.data_as(_P)))
+        return added
+
+    def counts(self):
+        """(56 raw cells, (6, 6) classes) of everything appended so far."""
+        cells = np.zeros(56, np.uint64)
+        out = np.zeros(36, np.uint64)
+        _check(_lib.tm_stream_counts(self._h, cells.ctypes.data_as(_P), out.ctypes.data_as(_P)))
+        return cells, out.reshape(6, 6)
+
+    @property
+    def edges(self):
+        return int(_lib.tm_stream_edges(self._h))
+
+    @property
+    def tail(self):
+        return int(_lib.tm_stream_tail(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tm_stream_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def split_cells(cells):
     cells = np.asarray(cells, np.uint64).reshape(56)
     return cells[:24].reshape(3, 2, 2, 2), cells[24:32].reshape(2, 2, 2), cells[32:].reshape(3, 2, 2, 2)
@@ -426,6 +484,33 @@ def tm_merge(cells):
     out = np.zeros(36, np.uint64)
     bad = _check(_lib.tm_merge(c.ctypes.data_as(_P), out.ctypes.data_as(_P)))
     return out.reshape(6, 6), bad
+
+
+def tm_count_shard(g, delta, owner, rank):
+    """56 raw cells of the centres u with owner[u] == rank (Tri type II only;
+    types I/III zero until tm_fill_tri_types of the sum over the ranks)."""
+    o, keep = _ptr(owner, np.int32)
+    if len(owner) != g.n:
+        raise ValueError("owner must have one entry per node")
+    cells = np.zeros(56, np.uint64)
+    _check(_lib.tm_count_shard(g.handle, int(delta), o, int(rank), cells.ctypes.data_as(_P)))
+    return cells
+
+
+def tm_fill_tri_types(cells):
+    """The 56 cells with their Tri type-I/III cells filled from type II (a
+    new uint64 array)."""
+    c = np.array(cells, np.uint64).reshape(56)
+    _check(_lib.tm_fill_tri_types(c.ctypes.data_as(_P)))
+    return c
+
+
+def tm_kernel_arch():
+    """Compute capability the library's kernels run as on the current device
+    (103 on a GB300)."""
+    a = ctypes.c_int32(0)
+    _check(_lib.tm_kernel_arch(ctypes.byref(a)))
+    return int(a.value)
 
 
 def tm_layout():
@@ -473,5 +558,8 @@ batch_config = tm_batch_config
 batch_get_config = tm_batch_get_config
 tune_batch = tm_tune_batch
 merge = tm_merge
+fill_tri_types = tm_fill_tri_types
+count_shard = tm_count_shard
+kernel_arch = tm_kernel_arch
 layout = tm_layout
 launch_count = tm_launch_count

@@ -91,11 +91,19 @@ def test_build_many_rejects_bad_component(tm):
 def test_count_select_and_multi(tm):
     s, d, t = synth.hub(scale=0.001)
     g = tm.build(s, d, t)
-    S, P, Q = tm.count_raw(g, 3600)
+    # the oracle's counters (Algorithm 1: Star and Pair; Algorithm 2: Tri)
+    S, P, Q = oracle.count(s, d, t, 3600)
     s1, p1, q1 = tm.count_select(g, 3600, tm.SELECT_STAR_PAIR)
     assert (s1 == S).all() and (p1 == P).all() and q1.sum() == 0
     s2, p2, q2 = tm.count_select(g, 3600, tm.SELECT_TRI)
     assert s2.sum() == 0 and p2.sum() == 0 and (q2 == Q).all()
+    s3, p3, q3 = tm.count_select(g, 3600, tm.SELECT_STAR_PAIR | tm.SELECT_TRI)
+    assert (s3 == S).all() and (p3 == P).all() and (q3 == Q).all()
+    for dl in (0, 600, 86400):
+        S, P, Q = oracle.count(s, d, t, dl)
+        s1, p1, _ = tm.count_select(g, dl, tm.SELECT_STAR_PAIR)
+        _, _, q2 = tm.count_select(g, dl, tm.SELECT_TRI)
+        assert (s1 == S).all() and (p1 == P).all() and (q2 == Q).all(), dl
     deltas = [0, 60, 600, 3600, 86400, 10 ** 7]
     multi = tm.count_multi(g, deltas)
     for i, dl in enumerate(deltas):

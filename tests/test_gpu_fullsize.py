@@ -1,7 +1,12 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times (tm_build + whole-graph tm_count on one GPU).
 
-The oracle cannot count a 60M-edge graph in seconds, so these tests check:
+  * whole graph: all 56 raw cells and the 36 classes of tm_count_raw /
+    tm_count (the path bench.py times) against the oracle's cells for the same
+    graph, stored in tests/golden/fullsize_*.json by
+    tests/golden/make_fullsize_golden.py (literal Algorithm 1 and 2 over host
+    threads; the file records the fingerprint of the input it counted, which
+    the test checks before comparing);
   * sampled outputs: the per-centre counters of the CUDA path
     (tm_count_centres) against the oracle's Algorithm 1 / Algorithm 2 at the
     same centres (Star, Pair and Tri type II, which are per-centre exact), for
@@ -11,6 +16,9 @@ The oracle cannot count a 60M-edge graph in seconds, so these tests check:
     cell by cell onto the original counts, and the pair-mirror / triangle
     triple equalities hold.
 """
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 
@@ -33,6 +41,32 @@ def tm():
 
 
 _CACHE = {}
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+def golden(name):
+    with open(GOLDEN / f"fullsize_{name}.json") as f:
+        return json.load(f)
+
+
+def check_golden(tm, name, deltas):
+    """tm_count_raw and tm_count of the whole graph against the oracle's
+    stored cells, bit for bit."""
+    gold = golden(name)
+    s, d, t = workload(name)
+    assert synth.fingerprint(s, d, t) == gold["fingerprint"], \
+        "the generator produced another graph than the one the oracle counted"
+    g = tm.build(dev(s), dev(d), dev(t))
+    try:
+        for delta in deltas:
+            want = gold["counts"][str(delta)]
+            star, pair, tri = tm.count_raw(g, delta)
+            assert star.ravel().tolist() == want["star"], delta
+            assert pair.ravel().tolist() == want["pair"], delta
+            assert tri.ravel().tolist() == want["tri"], delta
+            assert tm.count(g, delta).ravel().tolist() == want["classes"], delta
+    finally:
+        g.free()
 
 
 def workload(name):
@@ -101,6 +135,10 @@ def check_centres(tm, s, d, t, delta, centres, key):
         g.free()
 
 
+def test_large_60M_whole_graph_equals_oracle(tm):
+    check_golden(tm, "large", [86400])
+
+
 def test_large_60M_full_size(tm):
     s, d, t = workload("large")
     assert len(s) == 60_000_000
@@ -108,9 +146,16 @@ def test_large_60M_full_size(tm):
     check_centres(tm, s, d, t, 86400, sample_centres(s, d), "oracle_large")
 
 
-@pytest.mark.parametrize("delta", [600, 86400])
+@pytest.mark.parametrize("delta", [600, 3600, 86400])
 def test_hub_30M_full_size(tm, delta):
     s, d, t = workload("hub")
     assert len(s) == 30_000_000
     check_invariants(tm, s, d, t, delta)
-    check_centres(tm, s, d, t, delta, sample_centres(s, d, k_per_band=4, seed=1), "oracle_hub")
+    centres = sample_centres(s, d, k_per_band=4, seed=1)
+    if delta == 600:
+        # two of the 16 hubs (1M incident edges each): at delta = 600 a hub's
+        # window holds about 60 entries, so the oracle's per-centre count is
+        # about linear in its degree
+        deg = np.bincount(np.concatenate([s, d]))
+        centres += [int(u) for u in np.argsort(-deg, kind="stable")[:2]]
+    check_centres(tm, s, d, t, delta, centres, "oracle_hub")

@@ -242,3 +242,8 @@ def test_time_ordered_input(tm):
         a = gpu_cells(tm, ss, dd, ts, delta)[3]
         b = gpu_cells(tm, ss[sh], dd[sh], ts[sh], delta)[3]
         assert (a == b).all()
+
+
+def test_kernels_run_as_sm103(tm):
+    """The library's kernels are sm_103a code, as the runtime reports them."""
+    assert tm.kernel_arch() == 103

@@ -1,12 +1,13 @@
 """The serving loop: requests of different sizes arriving from several client
 threads, continuous batching, memory-budget admission with LRU eviction, and
 results that are the same alone and in the mix (tolerance 0: the counts are
-integers)."""
+integers) and equal to the oracle's counts of the same graph."""
 import threading
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2204_09236_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +35,21 @@ def alone(tm, graph, delta):
     out = tm.count(g, delta)
     g.free()
     return out
+
+
+_ORACLE = {}
+
+
+def oracle_classes(key, graph, delta):
+    """The oracle's 36 class counts of `graph` (literal Algorithm 1 and 2 on
+    every host core), cached per (graph, delta)."""
+    if (key, delta) not in _ORACLE:
+        if key not in _ORACLE:
+            _ORACLE[key] = oracle.Graph(*graph)
+        out, bad = oracle.merge(*_ORACLE[key].count_mt(delta))
+        assert bad == 0
+        _ORACLE[(key, delta)] = out
+    return _ORACLE[(key, delta)]
 
 
 def test_results_same_alone_and_in_the_mix(tm):
@@ -69,6 +85,7 @@ def test_results_same_alone_and_in_the_mix(tm):
         if (k, d) not in cache:
             cache[(k, d)] = alone(tm, graphs[k], d)
         assert (out == cache[(k, d)]).all(), (rid, k, d)
+        assert (out == oracle_classes(("mix", k), graphs[k], d)).all(), (rid, k, d)
         assert lat >= 0
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
@@ -87,6 +104,7 @@ def test_budget_admission_and_eviction(tm):
     for rid, k in ids:
         out, _ = srv.wait(rid)
         assert (out == alone(tm, graphs[k], deltas[k])).all()
+        assert (out == oracle_classes(("budget", k), graphs[k], deltas[k])).all(), k
     st = srv.stats()
     assert st["evictions"] >= 1
     assert st["resident_bytes"] <= budget
