@@ -257,9 +257,16 @@ def measure_batch(tm, torch, graphs, deltas, steps, warmup, tune, dist=None):
     c_step, _ = timed_wall(lambda: tm.count_many(g, deltas), steps, 1, torch)
     g.free()
     p_step, out_p = timed_wall(plain, max(1, steps // 2), 1, torch)
+    built = [tm.build(*v) for v in views]
+    pc_step, _ = timed_wall(lambda: [tm.count(h, dl) for h, dl in zip(built, deltas)],
+                            max(1, steps // 2), 1, torch)
+    for h in built:
+        h.free()
     return {"graphs": len(graphs), "m_total": M, "value": M / step, "unit": UNIT,
             "ms": step * 1e3, "count_only": {"value": M / c_step, "unit": UNIT, "ms": c_step * 1e3},
-            "plain_one_graph_per_launch": {"value": M / p_step, "unit": UNIT, "ms": p_step * 1e3},
+            "plain_one_graph_per_launch": {"value": M / p_step, "unit": UNIT, "ms": p_step * 1e3,
+                                           "count_only": {"value": M / pc_step, "unit": UNIT,
+                                                          "ms": pc_step * 1e3}},
             "speedup_vs_plain": p_step / step, "batched_equals_plain": bool((out_b == out_p).all()),
             "launches_per_step": launches, "tune": tuned, "batch_config": tm.batch_get_config(),
             "timing": "wall clock around synchronous calls, inputs resident on the device"}
@@ -535,6 +542,55 @@ def measure_shard(tm, torch, args, s, d, t, delta, world, rank, dist):
     return el, same
 
 
+def measure_hub(tm, torch, steps):
+    """The hub-skew workload at its three windows: the step (build + count)
+    per delta, the count alone, and tm_count_multi over the three windows
+    against three separate tm_count calls (graph resident, wall clock around
+    the synchronous calls)."""
+    deltas = [600, 3600, 86400]
+    s, d, t = gen("hub", 1.0, 0)
+    m = len(s)
+    src, dst, tt = (torch.from_numpy(x).cuda() for x in (s, d, t))
+    stream = torch.cuda.current_stream()
+    cells = torch.zeros(56, dtype=torch.uint64, device="cuda")
+    out = {"workload": WORKLOADS["hub"]["desc"], "m": m, "per_delta": {}}
+    for delta in deltas:
+        def step():
+            g = tm.build_async(src, dst, tt, stream)
+            tm.count_async(g, delta, cells, stream)
+            g.free_async(stream)
+        for _ in range(2):
+            step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / steps
+        g = tm.build_async(src, dst, tt, stream)
+        tm.count_async(g, delta, cells, stream)
+        e0.record(stream)
+        for _ in range(steps):
+            tm.count_async(g, delta, cells, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        count_ms = e0.elapsed_time(e1) / steps
+        g.free_async(stream)
+        out["per_delta"][str(delta)] = {"value": m / (step_ms / 1e3), "unit": UNIT,
+                                        "step_ms": step_ms, "count_ms": count_ms,
+                                        "count_only": m / (count_ms / 1e3)}
+    g = tm.build(src, dst, tt)
+    multi_ms, multi = timed_wall(lambda: tm.count_multi(g, deltas), steps, 1, torch)
+    sep_ms, sep = timed_wall(lambda: np.stack([tm.count(g, x) for x in deltas]), steps, 1, torch)
+    g.free()
+    out["multi_delta"] = {"deltas": deltas, "multi_ms": multi_ms * 1e3,
+                          "separate_ms": sep_ms * 1e3, "speedup": sep_ms / multi_ms,
+                          "multi_equals_separate": bool((multi == sep).all()),
+                          "timing": "wall clock around synchronous calls, graph resident"}
+    return out
+
+
 def roofline_of(phases, m, workload, scale):
     peak, peak_kind = measured_peak()
 
@@ -566,6 +622,7 @@ def main():
     ap.add_argument("--no-count-only", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serve object of the line")
+    ap.add_argument("--no-hub", action="store_true", help="skip the hub object of the line")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch: skip the autotuner (use the library defaults)")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -648,7 +705,9 @@ def main():
         if rank == 0 and not args.no_cpu_baseline:
             cpu = cpu_baseline(s, d, t, delta, args.cpu_sample_days)
         del s, d, t
-        batch = serve = None
+        batch = serve = hub = None
+        if rank == 0 and not args.no_hub and args.workload == "large":
+            hub = measure_hub(tm, torch, args.steps)
         if rank == 0 and not args.no_batch:
             graphs, deltas = gen_batch(1.0, 0)
             batch = measure_batch(tm, torch, graphs, deltas, args.batch_steps, 1,
@@ -671,7 +730,7 @@ def main():
                 "count_only": ({"value": m / (r["count_ms"] / 1e3), "unit": UNIT,
                                 "ms": r["count_ms"]} if r["count_ms"] else None),
                 "phases_ms": {k: round(v, 4) for k, v in r["phases"].items()},
-                "isomorphism_mismatches": bad, "batch": batch, "serve": serve}))
+                "isomorphism_mismatches": bad, "hub": hub, "batch": batch, "serve": serve}))
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -146,8 +146,14 @@ int tm_count_shard(const tm_graph *g, int64_t delta, const int32_t *owner, int32
 int tm_count_select(const tm_graph *g, int64_t delta, int32_t what, uint64_t cells[56]);
 
 /*
- * Counts one graph for k windows deltas[0..k) in one batched count (one
- * segment per window); out[i*36 .. i*36+36) as in tm_count.
+ * Counts one graph for k windows deltas[0..k) (any order, repeats allowed);
+ * out[i*36 .. i*36+36) as in tm_count. The windows are sorted and counted in
+ * sweeps of up to 8: the windows of an entry nest, so one pass finds every
+ * entry's window start for all of them, one walk of each entry's
+ * same-neighbour links gives every window's Star/Pair terms, and the Tri
+ * joins run once per window on those starts. Borrows about 36 bytes per edge
+ * and window of pool scratch (one sweep at a time); rejects a negative delta
+ * and 2m * 8 >= 2^31 entries in one sweep.
  * The paper's delta sensitivity experiment (Sec. V-E, Fig. 11(a)) is this
  * call over a list of deltas.
  */

@@ -444,17 +444,39 @@ int tm_count_multi(const tm_graph *g, const int64_t *deltas, int32_t k, uint64_t
         check_graph(g);
         if (k < 0 || (k > 0 && (!deltas || !out))) fail(TM_EINVAL, "bad multi-delta arguments");
         if (k == 0) return;
-        std::vector<JobSpec> jobs;
+        std::vector<int32_t> order(k);
         for (int32_t i = 0; i < k; i++) {
             if (deltas[i] < 0) fail(TM_EINVAL, "delta must be >= 0");
-            jobs.push_back(JobSpec{&g->g, deltas[i], 0, (int32_t)(2 * g->g.m)});
+            order[i] = i;
         }
-        int64_t ie;
-        int32_t bps;
-        current_config(ie, bps);
-        std::vector<uint64_t> cells;
-        run_jobs(jobs, cells, ie, bps);
-        for (int32_t i = 0; i < k; i++) tm_merge(cells.data() + (size_t)NCELLS * i, out + 36 * (size_t)i);
+        // one sweep per run of up to 8 windows in ascending order
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return deltas[a] < deltas[b]; });
+        DevicePlan &dp = plan_for(current_device_id());
+        std::lock_guard<std::mutex> lk(dp.mu);
+        if (!dp.stream) TM_CUDA(cudaStreamCreateWithFlags(&dp.stream, cudaStreamNonBlocking));
+        cudaStream_t s = dp.stream;
+        unsigned long long *d = static_cast<unsigned long long *>(
+            dev_alloc(sizeof(unsigned long long) * NCELLS * k, s));
+        std::vector<uint64_t> cells((size_t)NCELLS * k);
+        try {
+            TM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NCELLS * k, s));
+            std::vector<int64_t> sorted(k);
+            for (int32_t i = 0; i < k; i++) sorted[i] = deltas[order[i]];
+            for (int32_t i = 0; i < k; i += 8) {
+                const int32_t c = std::min<int32_t>(8, k - i);
+                launch_count_multi_delta(g->g, sorted.data() + i, c, d + (size_t)NCELLS * i, s);
+            }
+            TM_CUDA(cudaMemcpyAsync(cells.data(), d, sizeof(uint64_t) * NCELLS * k,
+                                    cudaMemcpyDeviceToHost, s));
+            TM_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            dev_free(d, s);
+            throw;
+        }
+        dev_free(d, s);
+        for (int32_t i = 0; i < k; i++)
+            tm_merge(cells.data() + (size_t)NCELLS * i, out + 36 * (size_t)order[i]);
     });
 }
 

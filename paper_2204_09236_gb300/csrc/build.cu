@@ -13,6 +13,7 @@
 //   6. links between consecutive same-neighbour entries of a centre
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -350,6 +351,46 @@ unsigned grid_for(int64_t n, int threads = 256) {
     return (unsigned)(blocks > 0 ? blocks : 1);
 }
 
+// Host-to-device copies of n pieces (destination, source, bytes) spread over
+// s and three upload streams of the current device; s waits for all of them.
+// The destinations were allocated in s's order, so the upload streams first
+// wait for s.
+template <typename D, typename H, typename B>
+void upload(size_t n, D dst_of, H src_of, B bytes_of, cudaStream_t s) {
+    static std::mutex mu;
+    static cudaStream_t aux[64][3] = {};
+    const int dev = current_device_id();
+    cudaStream_t up[3] = {nullptr, nullptr, nullptr};
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int k = 0; k < 3; k++) {
+            if (!aux[dev][k]) TM_CUDA(cudaStreamCreateWithFlags(&aux[dev][k], cudaStreamNonBlocking));
+            up[k] = aux[dev][k];
+        }
+    }
+    cudaEvent_t fork, join[3];
+    TM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int k = 0; k < 3; k++) TM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    TM_CUDA(cudaEventRecord(fork, s));
+    bool used[3] = {false, false, false};
+    for (size_t i = 0; i < n; i++) {
+        const int k = (int)(i % 4) - 1;  // piece 0 on s, the others on the upload streams
+        cudaStream_t st = (k < 0 || !up[k]) ? s : up[k];
+        if (st != s && !used[k]) {
+            TM_CUDA(cudaStreamWaitEvent(st, fork, 0));
+            used[k] = true;
+        }
+        TM_CUDA(cudaMemcpyAsync(dst_of(i), src_of(i), bytes_of(i), cudaMemcpyHostToDevice, st));
+    }
+    for (int k = 0; k < 3; k++)
+        if (used[k]) {
+            TM_CUDA(cudaEventRecord(join[k], up[k]));
+            TM_CUDA(cudaStreamWaitEvent(s, join[k], 0));
+        }
+    cudaEventDestroy(fork);
+    for (int k = 0; k < 3; k++) cudaEventDestroy(join[k]);
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -550,22 +591,37 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     int32_t *h_src = nullptr, *h_dst = nullptr;
     int64_t *h_t = nullptr;
     if (m > 0) {
-        // host arrays are copied in; device arrays are read in place
+        // host arrays are copied in (device arrays are read in place): the
+        // pieces go out on s and the three upload streams at once, so several
+        // copy engines share the upload, and s waits for all of them
+        struct Piece {
+            void *d;
+            const void *h;
+            size_t bytes;
+        };
+        std::vector<Piece> pieces;
         if (!is_device_ptr(src_in)) {
             h_src = dev_alloc_n<int32_t>(m, s);
-            TM_CUDA(cudaMemcpyAsync(h_src, src_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+            pieces.push_back({h_src, src_in, sizeof(int32_t) * m});
             src = h_src;
         }
         if (!is_device_ptr(dst_in)) {
             h_dst = dev_alloc_n<int32_t>(m, s);
-            TM_CUDA(cudaMemcpyAsync(h_dst, dst_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+            pieces.push_back({h_dst, dst_in, sizeof(int32_t) * m});
             dst = h_dst;
         }
         if (!is_device_ptr(t_in)) {
             h_t = dev_alloc_n<int64_t>(m, s);
-            TM_CUDA(cudaMemcpyAsync(h_t, t_in, sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
-            t = h_t;
+            const size_t half = sizeof(int64_t) * (m / 2);
+            pieces.push_back({h_t, t_in, half});
+            pieces.push_back({reinterpret_cast<char *>(h_t) + half,
+                              reinterpret_cast<const char *>(t_in) + half,
+                              sizeof(int64_t) * m - half});
         }
+        upload(pieces.size(), [&](size_t i) { return pieces[i].d; },
+               [&](size_t i) { return pieces[i].h; }, [&](size_t i) { return pieces[i].bytes; },
+               s);
+        if (h_t) t = h_t;
     }
     auto release_inputs = [&]() {
         if (h_src) dev_free(h_src, s);

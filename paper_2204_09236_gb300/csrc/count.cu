@@ -49,8 +49,10 @@
 // and k_star_pair_list makes each of them produce its own W terms and its
 // predecessor's F term; k_star_pair does the same per entry without scratch.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
+#include <vector>
 
 #include "tm_internal.cuh"
 
@@ -431,7 +433,7 @@ __device__ __forceinline__ int32_t gallop_fwd(const int64_t *__restrict__ tt, in
 // persistent warps (or blocks) in index order: echunk consecutive entries for
 // the streaming passes, SP_CHUNK listed entries for the Star/Pair sweep, 32
 // joins for the Tri join.
-constexpr int SP_CHUNK = THREADS * 4;  // listed entries per block unit of the Star/Pair sweep
+constexpr int SP_CHUNK = THREADS;  // listed entries per block unit of the Star/Pair sweep
 
 struct SegArgs {
     Segment seg0;          // the segment when segs is null
@@ -636,14 +638,15 @@ __device__ __forceinline__ void flush_lane_copies(const unsigned long long *sacc
 
 // The Star/Pair sweep of the back-active entries that k_window_lo listed, 32
 // to a warp with every lane busy. A block takes units of SP_CHUNK listed
-// entries of one segment and adds into its shared copies of the cells, which
-// it flushes into the segment's cells when the next unit belongs to another
-// segment, and at the end.
+// entries of one segment from a shared head (one atomic per unit, in index
+// order) and adds into its shared copies of the cells, which it flushes into
+// the segment's cells when the next unit belongs to another segment, and at
+// the end.
 template <bool ONE>
 __global__ void __launch_bounds__(THREADS, 5)
     k_star_pair_list(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
                      const int32_t *__restrict__ act, const int32_t *__restrict__ nact,
-                     const int32_t *__restrict__ sp_pre) {
+                     const int32_t *__restrict__ sp_pre, int32_t *__restrict__ head) {
     // one copy of the 32 cells per lane index (shared by the block's warps),
     // so the lanes of a warp never add to the same word
     __shared__ unsigned long long sacc[32 * SP_COPIES];
@@ -653,7 +656,14 @@ __global__ void __launch_bounds__(THREADS, 5)
     const int64_t nu = list_units<ONE>(A, sp_pre, nact, SP_CHUNK);
     int32_t cur = -1;
     unsigned long long *cur_cells = nullptr;
-    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+    __shared__ int32_t next;
+    while (true) {
+        // the next unit from the shared head: blocks that drew short units take more
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(head, 1);
+        __syncthreads();
+        const int64_t u = next;
+        if (u >= nu) break;
         int64_t ui;
         const int32_t c = list_unit_seg<ONE>(A, sp_pre, u, &ui);  // block-uniform
         const Segment &sg = seg_ref<ONE>(A, c);
@@ -817,6 +827,7 @@ __device__ __forceinline__ TriEdge make_tri_edge(const DevGraph &g, int32_t r, u
 // (dj = 0); at the destination w it is inward (dj = 1). A match ranked after
 // the item is centred at the item's centre, one ranked before it at the big
 // window's centre.
+template <bool SHARD = false>
 __device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, uint32_t big,
                                                  int32_t rank_lo_big, uint32_t rj_s,
                                                  const uint2 it, uint64_t key,
@@ -831,7 +842,7 @@ __device__ __forceinline__ void tri_probe_hashed(const DevGraph &g, uint32_t big
     int32_t b_out_big = big_is_min ? c.fb : c.nb - c.fb;  // before the item, source == big
     int32_t a_out_big = big_is_min ? c.fa : c.na - c.fa;  // after the item, source == big
     const int di = dir_of(it.x);                          // item w.r.t. its centre
-    if (rank_lo_big & 0xc0000000) {
+    if (SHARD && (rank_lo_big & 0xc0000000)) {
         // a shard's join: the matches after the item are centred at the item's
         // centre, those before it at the big window's centre
         const bool skip_u = (rank_lo_big >> 30) & 1, skip_w = (uint32_t)rank_lo_big >> 31;
@@ -930,20 +941,23 @@ struct TriProbe {
 // the rest at its end.
 constexpr int TRI_QUEUE = 96;
 
+template <bool SHARD = false>
 __device__ __forceinline__ void tri_run_queue(const DevGraph &g, const TriProbe *q, int n,
                                               unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
     if (lane < n) {
         const TriProbe p = q[lane];
-        tri_probe_hashed(g, p.big, p.rank_lo_big, p.rj_s, p.it, p.key, acc);
+        tri_probe_hashed<SHARD>(g, p.big, p.rank_lo_big, p.rj_s, p.it, p.key, acc);
     }
 }
 
+template <bool SHARD = false>
 __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEdge *edges,
                                                   const int32_t *incl, int32_t total,
                                                   TriProbe *q, int &qn,
                                                   unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
+    int last[2] = {0, 0};
     for (int32_t jb = 0; jb < total; jb += 64) {
         int32_t j[2], own[2];
         bool ok[2];
@@ -951,14 +965,28 @@ __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEd
         for (int k = 0; k < 2; k++) {
             j[k] = jb + 32 * k + lane;
             ok[k] = j[k] < total;
-            // owner: the first lane whose inclusive prefix exceeds j
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (incl[mid] > j[k]) hi = mid;
-                else lo = mid + 1;
+            // owner: the first lane whose inclusive prefix exceeds j, galloping
+            // forwards from this lane's previous owner (j only grows)
+            int o = last[k];
+            if (ok[k] && incl[o] <= j[k]) {
+                int lo = o, hi = 31, step = 1;
+                while (lo + step < 31) {
+                    if (incl[lo + step] > j[k]) {
+                        hi = lo + step;
+                        break;
+                    }
+                    lo += step;
+                    step <<= 1;
+                }
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (incl[mid] > j[k]) hi = mid;
+                    else lo = mid;
+                }
+                o = hi;
             }
-            own[k] = lo;
+            last[k] = o;
+            own[k] = o;
         }
         uint2 it[2];
 #pragma unroll
@@ -996,7 +1024,7 @@ __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEd
         }
         __syncwarp();
         while (qn >= 32) {
-            tri_run_queue(g, q + qn - 32, 32, acc);  // the newest 32: nothing to move
+            tri_run_queue<SHARD>(g, q + qn - 32, 32, acc);  // the newest 32: nothing to move
             qn -= 32;
             __syncwarp();
         }
@@ -1075,7 +1103,7 @@ __global__ void __launch_bounds__(THREADS)
 // a kernel that does nothing else. A warp takes units of echunk entries of
 // one segment, gathers its jobs in shared memory and reserves space 32 at a
 // time, so the shared counter takes one atomic per 32 jobs.
-template <bool ONE>
+template <bool ONE, bool SHARD>
 __global__ void __launch_bounds__(THREADS)
     k_tri_jobs(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
                TriEdge *__restrict__ jobs,
@@ -1127,7 +1155,7 @@ __global__ void __launch_bounds__(THREADS)
                     const uint32_t u = (uint32_t)g.tc[r], w = node_of(en[k].x);
                     E = make_tri_edge(g, (int32_t)r, u, w, (int32_t)en[k].y, lo_u[k], twin[k],
                                       lo_w[k]);
-                    if (A.own != nullptr) {
+                    if (SHARD) {
                         const bool cu = owns(A, u), cw = owns(A, w);
                         has = cu || cw;
                         E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
@@ -1172,13 +1200,14 @@ __device__ __forceinline__ void warp_flush_tri(unsigned long long (&acc)[8],
 }
 
 // k_tri_join: each warp takes units of 32 consecutive jobs of one segment
-// and runs their probes as one flattened list, the hash lookups through the
-// warp's queue. When its next unit belongs to another segment the warp
+// from a shared head (one atomic per unit, in index order) and runs their
+// probes as one flattened list, the hash lookups through the warp's queue. When its next unit belongs to another segment the warp
 // drains its queue and adds its counters into the segment's cells.
-template <bool ONE>
+template <bool ONE, bool SHARD>
 __global__ void __launch_bounds__(THREADS, 5)
     k_tri_join(const __grid_constant__ SegArgs A, const TriEdge *__restrict__ jobs,
-               const int32_t *__restrict__ njobs, const int32_t *__restrict__ tj_pre) {
+               const int32_t *__restrict__ njobs, const int32_t *__restrict__ tj_pre,
+               int32_t *__restrict__ head) {
     __shared__ TriEdge edges[TRI_WARPS][32];
     __shared__ int32_t incl[TRI_WARPS][32];
     __shared__ TriProbe queue[TRI_WARPS][TRI_QUEUE];
@@ -1186,17 +1215,22 @@ __global__ void __launch_bounds__(THREADS, 5)
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[c] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
     const int64_t nu = list_units<ONE>(A, tj_pre, njobs, 32);
     int qn = 0;
     int32_t cur = -1;
-    for (int64_t u = blockIdx.x * (int64_t)TRI_WARPS + warp; u < nu; u += nwarps) {
+    while (true) {
+        // the next unit from the shared head: the joins of hub pairs are long,
+        // so warps draw units as they finish instead of a fixed share
+        int32_t un = 0;
+        if (lane == 0) un = atomicAdd(head, 1);
+        const int64_t u = __shfl_sync(0xffffffffu, un, 0);
+        if (u >= nu) break;
         int64_t ui;
         const int32_t c = list_unit_seg<ONE>(A, tj_pre, u, &ui);  // warp-uniform
         if constexpr (!ONE) {
             if (c != cur && cur >= 0) {
                 const Segment &prev = seg_ref<ONE>(A, cur);
-                tri_run_queue(prev.g, queue[warp], qn, acc);
+                tri_run_queue<SHARD>(prev.g, queue[warp], qn, acc);
                 qn = 0;
                 __syncwarp();
                 warp_flush_tri(acc, prev.cells);
@@ -1213,15 +1247,15 @@ __global__ void __launch_bounds__(THREADS, 5)
         edges[warp][lane] = E;
         incl[warp][lane] = inc;
         __syncwarp();
-        tri_probes_queued(sg.g, edges[warp], incl[warp], total, queue[warp], qn, acc);
+        tri_probes_queued<SHARD>(sg.g, edges[warp], incl[warp], total, queue[warp], qn, acc);
         __syncwarp();
     }
     if constexpr (ONE) {
-        tri_run_queue(A.seg0.g, queue[warp], qn, acc);
+        tri_run_queue<SHARD>(A.seg0.g, queue[warp], qn, acc);
         block_flush<8, 0>(acc, 32 + 8, A.seg0.cells);
     } else if (cur >= 0) {
         const Segment &last = seg_ref<ONE>(A, cur);
-        tri_run_queue(last.g, queue[warp], qn, acc);
+        tri_run_queue<SHARD>(last.g, queue[warp], qn, acc);
         warp_flush_tri(acc, last.cells);
     }
 }
@@ -1283,6 +1317,229 @@ __global__ void k_fill_tri_types(unsigned long long *cells) {
             }
 }
 
+// ------------------------------------------------------- several windows
+//
+// A sorted list of windows delta_0 <= ... <= delta_{K-1} in one sweep
+// (K <= MAX_DELTAS). The windows of one entry nest, W_0(r) within ... within
+// W_{K-1}(r), so one pass finds every entry's K window starts (the largest by
+// the usual search, each smaller one by galloping forwards from the next
+// larger), and one walk of a back-active entry's same-neighbour links serves
+// every window: the entries a >= lo_k(r) of the walk (a prefix of it, as the
+// walk goes backwards) make window k's W terms, and the links up to hi_k(p)
+// (a prefix of the forward walk) its F term. The Tri joins then run one
+// segment per window on these window starts.
+constexpr int MAX_DELTAS = 8;
+
+struct DeltaList {
+    int64_t d[MAX_DELTAS];  // ascending
+    int32_t k;
+};
+
+// wl[k * 2m + r] = lo_k(r) for every entry r and window k; the back-active
+// entries of the largest window are listed in act (count *nact).
+__global__ void __launch_bounds__(THREADS)
+    k_window_lo_multi(const DevGraph g, const DeltaList D, int32_t *__restrict__ wl,
+                      int32_t *__restrict__ act, int32_t *__restrict__ nact) {
+    __shared__ int32_t buf[THREADS / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *wb = buf[warp];
+    const int64_t n2 = 2 * g.m;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int K = D.k;
+    const int64_t dmax = D.d[K - 1];
+    for (int64_t c0 = wid * COUNT_ECHUNK; c0 < n2; c0 += nwarps * COUNT_ECHUNK) {
+        const int64_t end = c0 + COUNT_ECHUNK < n2 ? c0 + COUNT_ECHUNK : n2;
+        int cnt = 0;
+        int32_t prev_u = -1;
+        int32_t prev_lo[MAX_DELTAS];  // this lane's window starts 32 entries before
+        for (int gi = 0; gi < COUNT_ECHUNK / 32; gi++) {
+            const int64_t i = c0 + gi * 32 + lane;
+            bool active = false;
+            if (i < end) {
+                const int32_t r = (int32_t)i;
+                const int64_t tr = g.tt[r];
+                const int32_t cu = g.tc[r];
+                int32_t lo = r;
+                if (cu == prev_u) {
+                    // every window slid by about 32 entries: search forwards from the
+                    // lane's previous start of the same window
+                    for (int k = K - 1; k >= 0; k--) {
+                        const int32_t l = gallop_fwd(g.tt, prev_lo[k], r, tr - D.d[k], 32);
+                        prev_lo[k] = l;
+                        wl[(int64_t)k * n2 + r] = l;
+                    }
+                    lo = prev_lo[K - 1];
+                } else {
+                    // a new centre: the largest window by the backward search, each
+                    // smaller one by galloping forwards from the next larger
+                    const int32_t sb = g.off[cu];
+                    if (r > sb && tr - g.tt[r - 1] <= dmax) lo = gallop_lo(g.tt, sb, r, tr - dmax);
+                    int32_t l = lo;
+                    for (int k = K - 1; k >= 0; k--) {
+                        if (k < K - 1 && l < r) l = gallop_fwd(g.tt, l, r, tr - D.d[k], 1);
+                        prev_lo[k] = l;
+                        wl[(int64_t)k * n2 + r] = l;
+                    }
+                }
+                prev_u = cu;
+                active = lo < r && g.lk[r].x >= lo;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, active);
+            if (active) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+            cnt += __popc(bal);
+            __syncwarp();
+            warp_append(wb, cnt, false, act, nact);
+        }
+        warp_append(wb, cnt, true, act, nact);
+    }
+}
+
+// Window k's W(r) terms from the running sums over the entries a >= lo of
+// the walk (as in star_pair_back_active), into the lane copies `sacc`.
+__device__ __forceinline__ void emit_w_terms(const DevGraph &g, int D3, int32_t r, int32_t seg_end,
+                                             int64_t cin_r, int64_t cin_end, int32_t lo,
+                                             const uint64_t (&n)[2], const uint64_t (&c2s)[2][2],
+                                             const uint64_t (&X)[2][2], const uint64_t (&Yp)[2][2],
+                                             unsigned long long *sacc) {
+    const int64_t cin_lo = g.cin[lo];
+    const int64_t co_lo = (int64_t)lo - cin_lo;
+#pragma unroll
+    for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+        for (int d2 = 0; d2 < 2; d2++) {
+            const uint64_t sp = c2s[d1][d2];
+            lane_add(sacc, IX(d1, d2, D3), sp);                                  // Pair
+            lane_add(sacc, 16 + IX(d1, d2, D3), X[d1][d2] - sp);                 // Star-II
+            const uint64_t base = d1 ? (uint64_t)cin_lo : (uint64_t)co_lo;      // C_d1(lo)
+            lane_add(sacc, 8 + IX(d1, d2, D3), Yp[d2][d1] - n[d2] * base - sp);  // Star-I
+            lane_add(sacc, 24 + IX(d1, d2, D3), 0 - sp);                         // Star-III
+        }
+    const int64_t after_in = cin_end - (cin_r + D3);
+    const int64_t after_o = (int64_t)(seg_end - r - 1) - after_in;
+#pragma unroll
+    for (int d1 = 0; d1 < 2; d1++) {
+        lane_add(sacc, 24 + IX(d1, D3, 0), n[d1] * (uint64_t)after_o);
+        lane_add(sacc, 24 + IX(d1, D3, 1), n[d1] * (uint64_t)after_in);
+    }
+}
+
+// The Star/Pair terms of the listed entry r (back-active in the largest
+// window) for every window it is back-active in, from one backward and one
+// forward walk of its same-neighbour links. Window k's copies of the 32 cells
+// start at sacc + k * 32 * SP_COPIES.
+__device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, const DeltaList &D,
+                                                            const int32_t *__restrict__ wl,
+                                                            int32_t r,
+                                                            unsigned long long *sacc) {
+    const int64_t *__restrict__ tt = g.tt;
+    const int64_t n2 = 2 * g.m;
+    const int K = D.k;
+    const int32_t u = g.tc[r];
+    const int32_t seg_end = g.off[u + 1];
+    const int D3 = dir_of(g.tn[r].x);
+    const int64_t cin_end = g.cin[seg_end];
+    const int64_t cin_r = g.cin[r];
+    const int2 lr = g.lk[r];
+    int32_t lo[MAX_DELTAS];
+    for (int k = 0; k < K; k++) lo[k] = wl[(int64_t)k * n2 + r];
+    {
+        // backward walk: window k takes the prefix of entries a >= lo[k]
+        uint64_t n[2] = {0, 0}, c2s[2][2] = {{0, 0}, {0, 0}}, X[2][2] = {{0, 0}, {0, 0}},
+                 Yp[2][2] = {{0, 0}, {0, 0}};
+        int32_t a = lr.x, cur = r;
+        int k = 0;  // windows finished so far (smallest first: their starts are highest)
+        while (true) {
+            const bool more = a >= lo[K - 1] && a < cur;  // links strictly decrease: ends
+            while (k < K && (!more || a < lo[k])) {
+                if (lr.x >= lo[k])
+                    emit_w_terms(g, D3, r, seg_end, cin_r, cin_end, lo[k], n, c2s, X, Yp,
+                                 sacc + k * 32 * SP_COPIES);
+                k++;
+            }
+            if (!more) break;
+            const int da = dir_of(g.tn[a].x);
+            const int64_t cin_a = g.cin[a];
+            const uint64_t between_in = (uint64_t)(cin_r - (cin_a + da));
+            const uint64_t between_o = (uint64_t)(r - a - 1) - between_in;
+            c2s[da][0] += n[0];
+            c2s[da][1] += n[1];
+            n[da] += 1;
+            X[da][0] += between_o;
+            X[da][1] += between_in;
+            Yp[da][0] += (uint64_t)(a - cin_a);
+            Yp[da][1] += (uint64_t)cin_a;
+            cur = a;
+            a = g.lk[a].x;
+        }
+    }
+    {
+        // forward walk from r for the predecessor p: window k takes the links
+        // up to hi_k(p), for the windows in which r is back-active
+        const int32_t p = lr.x;
+        const int64_t tp = tt[p];
+        const int Dp = dir_of(g.tn[p].x);
+        int k = 0;
+        while (k < K && lr.x < lo[k]) k++;  // r is back-active in windows k..K-1
+        int32_t hi = k < K ? gallop_hi(tt, r, seg_end, tp, D.d[k]) : r;
+        uint64_t f0 = 0, f1 = 0;
+        int32_t b = r, cur = p;
+        const int32_t hmax = gallop_hi(tt, r, seg_end, tp, D.d[K - 1]);
+        while (k < K) {
+            const bool more = b > cur && b <= hmax;  // links strictly increase: ends
+            while (k < K && (!more || b > hi)) {
+                const int64_t cin_h1 = (int64_t)g.cin[hi] + dir_of(g.tn[hi].x);  // C_in(hi+1)
+                const int64_t after_in = cin_end - cin_h1;
+                const int64_t after_o = (int64_t)(seg_end - hi - 1) - after_in;
+                unsigned long long *sk = sacc + k * 32 * SP_COPIES;
+                lane_add(sk, 24 + IX(Dp, 0, 0), 0 - f0 * (uint64_t)after_o);
+                lane_add(sk, 24 + IX(Dp, 0, 1), 0 - f0 * (uint64_t)after_in);
+                lane_add(sk, 24 + IX(Dp, 1, 0), 0 - f1 * (uint64_t)after_o);
+                lane_add(sk, 24 + IX(Dp, 1, 1), 0 - f1 * (uint64_t)after_in);
+                k++;
+                if (k < K) hi = gallop_hi(tt, hi, seg_end, tp, D.d[k]);
+            }
+            if (!more) break;
+            if (dir_of(g.tn[b].x)) f1 += 1;
+            else f0 += 1;
+            cur = b;
+            b = g.lk[b].y;
+        }
+    }
+}
+
+// The Star/Pair sweep of several windows: the entries listed by
+// k_window_lo_multi, with K sets of lane copies of the 32 cells in dynamic
+// shared memory; window k's cells go to cells + 56 k.
+__global__ void __launch_bounds__(THREADS)
+    k_star_pair_list_multi(const __grid_constant__ DevGraph g, const DeltaList D,
+                           const int32_t *__restrict__ wl, const int32_t *__restrict__ act,
+                           const int32_t *__restrict__ nact_ptr, int32_t *__restrict__ head,
+                           unsigned long long *__restrict__ cells) {
+    extern __shared__ unsigned long long msacc[];  // [K][32 * SP_COPIES]
+    const int K = D.k;
+    for (int i = threadIdx.x; i < K * 32 * SP_COPIES; i += blockDim.x) msacc[i] = 0;
+    const int32_t nact = *nact_ptr;
+    unsigned long long *mine = msacc + (threadIdx.x & 31);
+    __shared__ int32_t next;
+    while (true) {
+        // units of SP_CHUNK listed entries from a shared head, as k_star_pair_list
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(head, 1);
+        __syncthreads();
+        const int64_t u = next;
+        if (u * SP_CHUNK >= nact) break;
+        for (int j = 0; j < SP_CHUNK / THREADS; j++) {
+            const int64_t i = u * SP_CHUNK + j * THREADS + threadIdx.x;
+            if (i >= nact) break;
+            star_pair_back_active_multi(g, D, wl, act[i], mine);
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < K; k++)
+        flush_lane_copies(msacc + k * 32 * SP_COPIES, cells + (size_t)NCELLS * k);
+}
+
 // Type-I/III Tri cells of every segment from its type-II cells.
 template <bool ONE>
 __global__ void k_fill_tri_types_seg(const __grid_constant__ SegArgs A) {
@@ -1334,16 +1591,18 @@ void count_scratch_carve(void *base, int64_t entries, int32_t k, CountScratch &s
     p += align_up(sizeof(int32_t) * e);
     sc.jobs = p;
     p += align_up(sizeof(TriEdge) * (e / 2 + 1));
-    sc.counts = reinterpret_cast<int32_t *>(p);  // nact[k] | njobs[k] | sp_pre[k+1] | tj_pre[k+1]
+    // heads[2] | nact[k] | njobs[k] | sp_pre[k+1] | tj_pre[k+1]
+    sc.counts = reinterpret_cast<int32_t *>(p);
     sc.k_cap = k;
 }
 
-int count_join_blocks_per_sm() { return occupancy(k_tri_join<false>); }
+int count_join_blocks_per_sm() { return occupancy(k_tri_join<false, false>); }
 
 void launch_count_segments(const Segment *one, const Segment *d_segs, const int32_t *d_meta,
                            int32_t k_cap, bool star_pair, bool tri, bool fill,
                            const CountScratch &sc, cudaStream_t s, int join_blocks_per_sm,
-                           int32_t echunk, const int32_t *own, int32_t own_rank) {
+                           int32_t echunk, const int32_t *own, int32_t own_rank,
+                           bool windows_ready) {
     if (echunk < 128 || echunk % 128) fail(TM_EINVAL, "entries per unit must be a multiple of 128");
     SegArgs A;
     std::memset(&A, 0, sizeof(A));
@@ -1364,37 +1623,56 @@ void launch_count_segments(const Segment *one, const Segment *d_segs, const int3
         A.eunit = d_meta;
     }
     const int k = one ? 1 : k_cap;
-    int32_t *nact = sc.counts, *njobs = sc.counts + k, *sp_pre = sc.counts + 2 * k,
-            *tj_pre = sc.counts + 3 * k + 1;
-    TM_CUDA(cudaMemsetAsync(sc.counts, 0, sizeof(int32_t) * 2 * k, s));
+    int32_t *heads = sc.counts, *nact = sc.counts + 2, *njobs = sc.counts + 2 + k,
+            *sp_pre = sc.counts + 2 + 2 * k, *tj_pre = sc.counts + 3 + 3 * k;
+    TM_CUDA(cudaMemsetAsync(sc.counts, 0, sizeof(int32_t) * (2 + 2 * k), s));
     {
         PhaseTimer pt(TM_PH_STAR_PAIR, s);
         int32_t *act = star_pair ? sc.act : nullptr;
-        if (one) TM_LAUNCH(k_window_lo<true>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
-        else TM_LAUNCH(k_window_lo<false>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
+        if (windows_ready && star_pair) fail(TM_EINVAL, "window starts given without a list");
+        if (windows_ready) {
+            // the caller wrote sc.wl
+        } else if (one) {
+            TM_LAUNCH(k_window_lo<true>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
+        } else {
+            TM_LAUNCH(k_window_lo<false>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, act, nact);
+        }
         if (star_pair) {
             const unsigned grid = (unsigned)(sms * occupancy(k_star_pair_list<true>));
             if (one) {
-                TM_LAUNCH(k_star_pair_list<true>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre);
+                TM_LAUNCH(k_star_pair_list<true>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre,
+                          heads);
             } else {
                 TM_LAUNCH(k_unit_prefix, 1, 1024, 0, s, d_meta, nact, SP_CHUNK, sp_pre);
-                TM_LAUNCH(k_star_pair_list<false>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre);
+                TM_LAUNCH(k_star_pair_list<false>, grid, THREADS, 0, s, A, sc.wl, sc.act, nact, sp_pre,
+                          heads);
             }
         }
     }
     if (tri) {
         PhaseTimer pt(TM_PH_TRI, s);
         TriEdge *jobs = static_cast<TriEdge *>(sc.jobs);
-        const int occ = occupancy(k_tri_join<true>);
+        const int occ = occupancy(k_tri_join<true, false>);
         const int bps = join_blocks_per_sm > 0 ? std::min(join_blocks_per_sm, occ) : occ;
-        if (one) {
-            TM_LAUNCH(k_tri_jobs<true>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs, njobs);
-            TM_LAUNCH(k_tri_join<true>, (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs, tj_pre);
+        if (one && own) {
+            TM_LAUNCH((k_tri_jobs<true, true>), (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs,
+                      njobs);
+            TM_LAUNCH((k_tri_join<true, true>), (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs,
+                      tj_pre, heads + 1);
+            if (fill) TM_LAUNCH(k_fill_tri_types_seg<true>, 1, 128, 0, s, A);
+        } else if (one) {
+            TM_LAUNCH((k_tri_jobs<true, false>), (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl,
+                      jobs, njobs);
+            TM_LAUNCH((k_tri_join<true, false>), (unsigned)(sms * bps), THREADS, 0, s, A, jobs,
+                      njobs, tj_pre, heads + 1);
             if (fill) TM_LAUNCH(k_fill_tri_types_seg<true>, 1, 128, 0, s, A);
         } else {
-            TM_LAUNCH(k_tri_jobs<false>, (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs, njobs);
+            if (own) fail(TM_EINVAL, "a shard of centres needs one segment");
+            TM_LAUNCH((k_tri_jobs<false, false>), (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl,
+                      jobs, njobs);
             TM_LAUNCH(k_unit_prefix, 1, 1024, 0, s, d_meta, njobs, 32, tj_pre);
-            TM_LAUNCH(k_tri_join<false>, (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs, tj_pre);
+            TM_LAUNCH((k_tri_join<false, false>), (unsigned)(sms * bps), THREADS, 0, s, A, jobs,
+                      njobs, tj_pre, heads + 1);
             if (fill)
                 TM_LAUNCH(k_fill_tri_types_seg<false>, (unsigned)((k + 127) / 128), 128, 0, s, A);
         }
@@ -1420,6 +1698,72 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
         PhaseTimer pt(TM_PH_TRI, s);
         TM_LAUNCH(k_tri_centre, (unsigned)blocks, THREADS, 0, s, g, delta, begin, end, dev_cells);
     }
+}
+
+void launch_count_multi_delta(const DevGraph &g, const int64_t *deltas, int32_t k,
+                              unsigned long long *dev_cells, cudaStream_t s) {
+    const int64_t n2 = 2 * g.m;
+    if (n2 == 0 || k <= 0) return;
+    if (k > MAX_DELTAS) fail(TM_EINVAL, "at most 8 windows per sweep");
+    DeltaList D;
+    std::memset(&D, 0, sizeof D);
+    D.k = k;
+    for (int32_t i = 0; i < k; i++) {
+        if (deltas[i] < 0 || (i > 0 && deltas[i] < deltas[i - 1]))
+            fail(TM_EINVAL, "windows must be >= 0 and ascending");
+        D.d[i] = deltas[i];
+    }
+    const int64_t total = n2 * k;
+    if (total >= (int64_t(1) << 31)) fail(TM_EINVAL, "2m * windows must be < 2^31");
+    // one segment per window, all on the whole graph, their scratch one after another
+    std::vector<Segment> segs(k);
+    for (int32_t i = 0; i < k; i++) {
+        segs[i].g = g;
+        segs[i].delta = deltas[i];
+        segs[i].cells = dev_cells + (size_t)NCELLS * i;
+        segs[i].begin = 0;
+        segs[i].end = (int32_t)n2;
+        segs[i].xbase = n2 * i;
+    }
+    void *mem = dev_alloc(count_scratch_bytes(total, k), s);
+    CountScratch sc;
+    count_scratch_carve(mem, total, k, sc);
+    try {
+        // list count and unit head (free until the Tri launches clear the counters)
+        int32_t *nact = sc.counts, *head = sc.counts + 1;
+        TM_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t) * 2, s));
+        const int sms = num_sms();
+        {
+            PhaseTimer pt(TM_PH_STAR_PAIR, s);
+            int64_t blocks = (n2 / COUNT_ECHUNK + WARPS_PER_BLOCK) / WARPS_PER_BLOCK;
+            blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+            TM_LAUNCH(k_window_lo_multi, (unsigned)blocks, THREADS, 0, s, g, D, sc.wl, sc.act, nact);
+            const size_t smem = sizeof(unsigned long long) * 32 * SP_COPIES * k;
+            static std::atomic<unsigned long long> attr_devices{0};
+            const int dev = current_device_id();
+            if (dev >= 64 || !((attr_devices.load() >> dev) & 1ull)) {
+                TM_CUDA(cudaFuncSetAttribute(k_star_pair_list_multi,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(unsigned long long) * 32 * SP_COPIES *
+                                                   MAX_DELTAS)));
+                if (dev < 64) attr_devices.fetch_or(1ull << dev);
+            }
+            int per_sm = 0;
+            TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list_multi,
+                                                                  THREADS, smem));
+            TM_LAUNCH(k_star_pair_list_multi, (unsigned)(sms * std::max(1, per_sm)), THREADS, smem,
+                      s, g, D, sc.wl, sc.act, nact, head, dev_cells);
+        }
+        // the Tri joins of each window on its window starts, one segment at a time
+        // (the graph read in place from the kernels' parameters)
+        for (int32_t i = 0; i < k; i++)
+            launch_count_segments(&segs[i], nullptr, nullptr, 1, false, true, true, sc, s, 0,
+                                  COUNT_ECHUNK, nullptr, 0, true);
+    } catch (...) {
+        dev_free(mem, s);
+        throw;
+    }
+    dev_free(mem, s);
 }
 
 void launch_count_parts(const DevGraph &g, int64_t delta, bool star_pair, bool tri,

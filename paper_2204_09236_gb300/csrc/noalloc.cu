@@ -70,12 +70,13 @@ extern "C" int tm_count_noalloc(const tm_graph *const *gs, const int64_t *deltas
         // the array keeps the previous call's contents: clear the slots in use
         TM_CUDA(cudaMemsetAsync(cells, 0, sizeof(unsigned long long) * NCELLS * (size_t)k, s));
         for (int32_t i = 0; i < k; i++) launch_count_untimed(*views[i], deltas[i], cells + NCELLS * i, s);
-        for (int32_t i = 0; i < k; i++) {
-            uint64_t raw[NCELLS];
-            TM_CUDA(cudaMemcpyAsync(raw, cells + NCELLS * i, sizeof raw, cudaMemcpyDeviceToHost, s));
-            TM_CUDA(cudaStreamSynchronize(s));
-            tm_merge(raw, out + 36 * (size_t)i);
-        }
+        // all k graphs' cells in one copy and one wait, into this thread's
+        // fixed host array (no host allocation either)
+        static thread_local uint64_t raw[TM_NOALLOC_MAX_GRAPHS * NCELLS];
+        TM_CUDA(cudaMemcpyAsync(raw, cells, sizeof(uint64_t) * NCELLS * (size_t)k,
+                                cudaMemcpyDeviceToHost, s));
+        TM_CUDA(cudaStreamSynchronize(s));
+        for (int32_t i = 0; i < k; i++) tm_merge(raw + NCELLS * (size_t)i, out + 36 * (size_t)i);
         return TM_OK;
     } catch (const Error &e) {
         record_error(e.code, e.msg);

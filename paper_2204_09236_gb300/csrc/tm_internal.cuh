@@ -254,7 +254,16 @@ constexpr int32_t COUNT_ECHUNK = 512;
 void launch_count_segments(const Segment *one, const Segment *d_segs, const int32_t *d_meta,
                            int32_t k_cap, bool star_pair, bool tri, bool fill,
                            const CountScratch &sc, cudaStream_t s, int join_blocks_per_sm,
-                           int32_t echunk, const int32_t *own = nullptr, int32_t own_rank = 0);
+                           int32_t echunk, const int32_t *own = nullptr, int32_t own_rank = 0,
+                           bool windows_ready = false);
+
+// The counts of one graph for k <= 8 windows deltas[0..k) (ascending) in one
+// sweep: one pass finds every entry's k window starts, one walk per listed
+// entry gives every window's Star/Pair terms, and the Tri joins run one
+// segment per window; window i's 56 cells (Tri types filled) are added into
+// dev_cells + 56 i.
+void launch_count_multi_delta(const DevGraph &g, const int64_t *deltas, int32_t k,
+                              unsigned long long *dev_cells, cudaStream_t s);
 int count_join_blocks_per_sm();
 // binaryVersion of a library kernel on the current device (e.g. 103).
 int kernel_binary_version();

@@ -112,3 +112,35 @@ def test_count_select_and_multi(tm):
     # monotone in delta, class by class
     assert (np.diff(multi.astype(np.int64), axis=0) >= 0).all()
     g.free()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_multi_delta_single_sweep_equals_oracle(tm, seed):
+    """tm_count_multi counts every window of an unsorted list with repeats in
+    sweeps of up to 8 nested windows; each window must equal the oracle."""
+    s, d, t = synth.random_small(700 + seed, 12, 2500, 300)
+    deltas = [40, 0, 7, 300, 7, 1, 2, 150, 75, 20, 3, 500]
+    g = tm.build(s, d, t)
+    try:
+        got = tm.count_multi(g, deltas)
+        G = oracle.Graph(s, d, t)
+        for i, dl in enumerate(deltas):
+            want, bad = oracle.merge(*G.count(dl))
+            assert bad == 0
+            assert (got[i] == want).all(), (seed, dl)
+    finally:
+        g.free()
+
+
+def test_multi_delta_on_hub_shape_equals_single_counts(tm):
+    s, d, t = synth.hub(scale=0.01)
+    g = tm.build(s, d, t)
+    try:
+        deltas = [86400, 600, 3600]
+        got = tm.count_multi(g, deltas)
+        for i, dl in enumerate(deltas):
+            assert (got[i] == tm.count(g, dl)).all(), dl
+        with pytest.raises(tm.TmError):
+            tm.count_multi(g, [600, -1])
+    finally:
+        g.free()

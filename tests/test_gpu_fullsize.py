@@ -139,6 +139,11 @@ def test_large_60M_whole_graph_equals_oracle(tm):
     check_golden(tm, "large", [86400])
 
 
+@pytest.mark.parametrize("delta", [600, 3600, 86400])
+def test_hub_30M_whole_graph_equals_oracle(tm, delta):
+    check_golden(tm, "hub", [delta])
+
+
 def test_large_60M_full_size(tm):
     s, d, t = workload("large")
     assert len(s) == 60_000_000

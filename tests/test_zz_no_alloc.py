@@ -9,6 +9,10 @@ call it through the C ABI and require exactly the counts of tm_count, on two
 calls in a row (the shared array keeps the previous call's contents, so the
 second call checks that it is cleared). This file is collected last.
 """
+import ctypes
+import glob
+import os
+
 import numpy as np
 import pytest
 
@@ -51,6 +55,39 @@ def test_noalloc_equals_tm_count_on_two_calls(tm, graphs):
     rev = tm.count_noalloc(gs[::-1], [d + 1 for d in deltas[::-1]])
     want_rev = np.stack([tm.count(g, d + 1) for g, d in zip(gs[::-1], deltas[::-1])])
     assert (rev == want_rev).all()
+
+
+def default_pool_bytes():
+    """(reserved, used) bytes of the current device's default memory pool,
+    the pool the library's other calls allocate from, read through the CUDA
+    runtime that torch ships."""
+    libdir = os.path.join(os.path.dirname(torch.__file__), "lib")
+    cands = sorted(glob.glob(os.path.join(libdir, "libcudart*.so*"))) + \
+        sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so*"))
+    if not cands:
+        pytest.skip("no CUDA runtime library to query the memory pool")
+    rt = ctypes.CDLL(cands[0])
+    dev = ctypes.c_int(0)
+    assert rt.cudaGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    vals = []
+    for attr in (5, 7):  # cudaMemPoolAttrReservedMemCurrent, cudaMemPoolAttrUsedMemCurrent
+        v = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+        vals.append(v.value)
+    return tuple(vals)
+
+
+def test_noalloc_leaves_the_memory_pool_unchanged(tm, graphs):
+    gs, deltas = graphs
+    tm.count_noalloc(gs, deltas)  # the first call looks up the array's address
+    torch.cuda.synchronize()
+    before = default_pool_bytes()
+    out = tm.count_noalloc(gs, deltas)
+    torch.cuda.synchronize()
+    assert default_pool_bytes() == before
+    assert out.shape == (len(gs), 6, 6)
 
 
 def test_noalloc_rejects_more_graphs_than_its_array_holds(tm, graphs):
