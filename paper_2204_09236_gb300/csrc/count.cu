@@ -1093,6 +1093,81 @@ __global__ void __launch_bounds__(THREADS)
     block_flush<8, 0>(acc, 32 + 8, cells);
 }
 
+constexpr int JOB_U = 4;  // groups of 32 entries per warp and step: chains of reads in flight
+
+// One step of k_tri_jobs: the joins of the source entries among the 32 * JOB_U
+// entries from base (below end) are added to the warp's buffer wb (cnt of
+// them, warp-uniform); full groups of 32 are appended to jobs (count *njobs).
+template <bool SHARD>
+__device__ __forceinline__ void tri_jobs_step(const SegArgs &A, const DevGraph &g,
+                                              const int32_t *__restrict__ swl, int64_t base,
+                                              int64_t end, TriEdge *wb, int &cnt,
+                                              TriEdge *__restrict__ jobs,
+                                              int32_t *__restrict__ njobs) {
+    const int lane = threadIdx.x & 31;
+    uint2 en[JOB_U];
+    int32_t lo_u[JOB_U], lo_w[JOB_U], twin[JOB_U];
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t r = base + k * 32 + lane;
+        en[k] = make_uint2(0x80000000u, 0);  // inward: no join
+        lo_u[k] = 0;
+        if (r < end) {
+            en[k] = g.tn[r];
+            lo_u[k] = swl[r];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t r = base + k * 32 + lane;
+        twin[k] = -1;
+        if (dir_of(en[k].x) == 0 && lo_u[k] < r) twin[k] = g.pos_dst[en[k].y];
+    }
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) lo_w[k] = twin[k] >= 0 ? swl[twin[k]] : 0;
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t r = base + k * 32 + lane;
+        bool has = twin[k] >= 0 && lo_w[k] < twin[k];
+        TriEdge E;
+        if (has) {
+            const uint32_t u = (uint32_t)g.tc[r], w = node_of(en[k].x);
+            E = make_tri_edge(g, (int32_t)r, u, w, (int32_t)en[k].y, lo_u[k], twin[k], lo_w[k]);
+            if (SHARD) {
+                const bool cu = owns(A, u), cw = owns(A, w);
+                has = cu || cw;
+                E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
+        cnt += __popc(bal);
+    }
+    __syncwarp();
+    while (cnt >= 32) {
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(njobs, 32);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        jobs[first + lane] = wb[cnt - 32 + lane];
+        cnt -= 32;
+        __syncwarp();
+    }
+}
+
+// The warp's last cnt (< 32) buffered joins appended to jobs.
+__device__ __forceinline__ void tri_jobs_flush(const TriEdge *wb, int cnt,
+                                               TriEdge *__restrict__ jobs,
+                                               int32_t *__restrict__ njobs) {
+    const int lane = threadIdx.x & 31;
+    if (cnt > 0) {
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(njobs, cnt);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (lane < cnt) jobs[first + lane] = wb[lane];
+    }
+    __syncwarp();
+}
+
 // Whole-graph Tri in two steps, with the window starts wl of k_window_lo.
 // k_tri_jobs: every edge (at its source entry) whose two windows are both
 // non-empty becomes one join, appended to its segment's range of `jobs`
@@ -1100,87 +1175,44 @@ __global__ void __launch_bounds__(THREADS)
 // adds its counts. Only a quarter of the edges have such a join on the large
 // workloads, so the joining warps below get full lists instead of sparse
 // ones, and the chain of dependent reads that finds a join is paid here, in
-// a kernel that does nothing else. A warp takes units of echunk entries of
-// one segment, gathers its jobs in shared memory and reserves space 32 at a
-// time, so the shared counter takes one atomic per 32 jobs.
+// a kernel that does nothing else. A warp gathers its jobs in shared memory
+// and reserves space 32 at a time, so the shared counter takes one atomic per
+// 32 jobs. On one graph the warps sweep steps of 32 * JOB_U entries strided
+// over the grid (all warps together stream one region of the arrays) and
+// flush once at the end; on a table a warp takes units of echunk entries of
+// one segment and flushes at the end of each unit.
 template <bool ONE, bool SHARD>
 __global__ void __launch_bounds__(THREADS)
     k_tri_jobs(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
-               TriEdge *__restrict__ jobs,
-               int32_t *__restrict__ njobs) {
-    constexpr int U = 4;  // groups of 32 entries per warp and step: U chains of reads in flight
-    __shared__ TriEdge buf[TRI_WARPS][32 * (U + 1)];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+               TriEdge *__restrict__ jobs, int32_t *__restrict__ njobs) {
+    __shared__ TriEdge buf[TRI_WARPS][32 * (JOB_U + 1)];
+    const int warp = threadIdx.x >> 5;
     TriEdge *wb = buf[warp];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
-    const int64_t nu = seg_units<ONE>(A);
-    for (int64_t u = wid; u < nu; u += nwarps) {
-        int64_t ui;
-        const int32_t c = unit_seg<ONE>(A, u, &ui);
-        const Segment &sg = seg_ref<ONE>(A, c);
-        const DevGraph &g = sg.g;
-        const int64_t c0 = sg.begin + ui * A.echunk;
-        const int64_t end = c0 + A.echunk < sg.end ? c0 + A.echunk : sg.end;
+    int cnt = 0;  // jobs held in wb (warp-uniform, < 32 between steps)
+    if constexpr (ONE) {
+        const Segment &sg = A.seg0;
         const int32_t *__restrict__ swl = wl + (sg.xbase - sg.begin);  // swl[r] = wl[x(r)]
         TriEdge *sjobs = jobs + sg.xbase / 2;
-        int cnt = 0;  // jobs held in wb (warp-uniform, < 32 between steps)
-        for (int64_t base = c0; base < end; base += 32 * U) {
-            uint2 en[U];
-            int32_t lo_u[U], lo_w[U], twin[U];
-#pragma unroll
-            for (int k = 0; k < U; k++) {
-                const int64_t r = base + k * 32 + lane;
-                en[k] = make_uint2(0x80000000u, 0);  // inward: no join
-                lo_u[k] = 0;
-                if (r < end) {
-                    en[k] = g.tn[r];
-                    lo_u[k] = swl[r];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < U; k++) {
-                const int64_t r = base + k * 32 + lane;
-                twin[k] = -1;
-                if (dir_of(en[k].x) == 0 && lo_u[k] < r) twin[k] = g.pos_dst[en[k].y];
-            }
-#pragma unroll
-            for (int k = 0; k < U; k++) lo_w[k] = twin[k] >= 0 ? swl[twin[k]] : 0;
-#pragma unroll
-            for (int k = 0; k < U; k++) {
-                const int64_t r = base + k * 32 + lane;
-                bool has = twin[k] >= 0 && lo_w[k] < twin[k];
-                TriEdge E;
-                if (has) {
-                    const uint32_t u = (uint32_t)g.tc[r], w = node_of(en[k].x);
-                    E = make_tri_edge(g, (int32_t)r, u, w, (int32_t)en[k].y, lo_u[k], twin[k],
-                                      lo_w[k]);
-                    if (SHARD) {
-                        const bool cu = owns(A, u), cw = owns(A, w);
-                        has = cu || cw;
-                        E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
-                    }
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, has);
-                if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
-                cnt += __popc(bal);
-            }
-            __syncwarp();
-            while (cnt >= 32) {
-                int32_t first = 0;
-                if (lane == 0) first = atomicAdd(njobs + c, 32);
-                first = __shfl_sync(0xffffffffu, first, 0);
-                sjobs[first + lane] = wb[cnt - 32 + lane];
-                cnt -= 32;
-                __syncwarp();
-            }
-        }
-        if (cnt > 0) {
-            int32_t first = 0;
-            if (lane == 0) first = atomicAdd(njobs + c, cnt);
-            first = __shfl_sync(0xffffffffu, first, 0);
-            if (lane < cnt) sjobs[first + lane] = wb[lane];
-            __syncwarp();
+        for (int64_t base = sg.begin + wid * (32 * JOB_U); base < sg.end;
+             base += nwarps * (32 * JOB_U))
+            tri_jobs_step<SHARD>(A, sg.g, swl, base, sg.end, wb, cnt, sjobs, njobs);
+        tri_jobs_flush(wb, cnt, sjobs, njobs);
+    } else {
+        const int64_t nu = seg_units<ONE>(A);
+        for (int64_t u = wid; u < nu; u += nwarps) {
+            int64_t ui;
+            const int32_t c = unit_seg<ONE>(A, u, &ui);
+            const Segment &sg = seg_ref<ONE>(A, c);
+            const int64_t c0 = sg.begin + ui * A.echunk;
+            const int64_t end = c0 + A.echunk < sg.end ? c0 + A.echunk : sg.end;
+            const int32_t *__restrict__ swl = wl + (sg.xbase - sg.begin);
+            TriEdge *sjobs = jobs + sg.xbase / 2;
+            for (int64_t base = c0; base < end; base += 32 * JOB_U)
+                tri_jobs_step<SHARD>(A, sg.g, swl, base, end, wb, cnt, sjobs, njobs + c);
+            tri_jobs_flush(wb, cnt, sjobs, njobs + c);
+            cnt = 0;
         }
     }
 }
@@ -1337,16 +1369,17 @@ struct DeltaList {
 
 // wl[k * 2m + r] = lo_k(r) for every entry r and window k; the back-active
 // entries of the largest window are listed in act (count *nact).
+template <int K>
 __global__ void __launch_bounds__(THREADS)
-    k_window_lo_multi(const DevGraph g, const DeltaList D, int32_t *__restrict__ wl,
-                      int32_t *__restrict__ act, int32_t *__restrict__ nact) {
+    k_window_lo_multi(const __grid_constant__ DevGraph g, const __grid_constant__ DeltaList D,
+                      int32_t *__restrict__ wl, int32_t *__restrict__ act,
+                      int32_t *__restrict__ nact) {
     __shared__ int32_t buf[THREADS / 32][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *wb = buf[warp];
     const int64_t n2 = 2 * g.m;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int K = D.k;
     const int64_t dmax = D.d[K - 1];
     for (int64_t c0 = wid * COUNT_ECHUNK; c0 < n2; c0 += nwarps * COUNT_ECHUNK) {
         const int64_t end = c0 + COUNT_ECHUNK < n2 ? c0 + COUNT_ECHUNK : n2;
@@ -1364,6 +1397,7 @@ __global__ void __launch_bounds__(THREADS)
                 if (cu == prev_u) {
                     // every window slid by about 32 entries: search forwards from the
                     // lane's previous start of the same window
+#pragma unroll
                     for (int k = K - 1; k >= 0; k--) {
                         const int32_t l = gallop_fwd(g.tt, prev_lo[k], r, tr - D.d[k], 32);
                         prev_lo[k] = l;
@@ -1376,6 +1410,7 @@ __global__ void __launch_bounds__(THREADS)
                     const int32_t sb = g.off[cu];
                     if (r > sb && tr - g.tt[r - 1] <= dmax) lo = gallop_lo(g.tt, sb, r, tr - dmax);
                     int32_t l = lo;
+#pragma unroll
                     for (int k = K - 1; k >= 0; k--) {
                         if (k < K - 1 && l < r) l = gallop_fwd(g.tt, l, r, tr - D.d[k], 1);
                         prev_lo[k] = l;
@@ -1428,33 +1463,52 @@ __device__ __forceinline__ void emit_w_terms(const DevGraph &g, int D3, int32_t 
 // window) for every window it is back-active in, from one backward and one
 // forward walk of its same-neighbour links. Window k's copies of the 32 cells
 // start at sacc + k * 32 * SP_COPIES.
+// The element k of a (register-resident) array, k known only at run time.
+template <int K>
+__device__ __forceinline__ int32_t pick(const int32_t (&a)[K], int k) {
+    int32_t v = a[0];
+#pragma unroll
+    for (int i = 1; i < K; i++)
+        if (k == i) v = a[i];
+    return v;
+}
+
+template <int K>
 __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, const DeltaList &D,
                                                             const int32_t *__restrict__ wl,
                                                             int32_t r,
                                                             unsigned long long *sacc) {
     const int64_t *__restrict__ tt = g.tt;
     const int64_t n2 = 2 * g.m;
-    const int K = D.k;
     const int32_t u = g.tc[r];
     const int32_t seg_end = g.off[u + 1];
     const int D3 = dir_of(g.tn[r].x);
     const int64_t cin_end = g.cin[seg_end];
     const int64_t cin_r = g.cin[r];
     const int2 lr = g.lk[r];
-    int32_t lo[MAX_DELTAS];
+    int32_t lo[K];
+#pragma unroll
     for (int k = 0; k < K; k++) lo[k] = wl[(int64_t)k * n2 + r];
     {
         // backward walk: window k takes the prefix of entries a >= lo[k]
-        uint64_t n[2] = {0, 0}, c2s[2][2] = {{0, 0}, {0, 0}}, X[2][2] = {{0, 0}, {0, 0}},
-                 Yp[2][2] = {{0, 0}, {0, 0}};
+        // running sums in scalars (as in star_pair_back_active), so that they stay
+        // in registers
+        uint64_t n0 = 0, n1 = 0, c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+        uint64_t X00 = 0, X01 = 0, X10 = 0, X11 = 0, Y00 = 0, Y01 = 0, Y10 = 0, Y11 = 0;
         int32_t a = lr.x, cur = r;
         int k = 0;  // windows finished so far (smallest first: their starts are highest)
         while (true) {
             const bool more = a >= lo[K - 1] && a < cur;  // links strictly decrease: ends
-            while (k < K && (!more || a < lo[k])) {
-                if (lr.x >= lo[k])
-                    emit_w_terms(g, D3, r, seg_end, cin_r, cin_end, lo[k], n, c2s, X, Yp,
+            while (k < K && (!more || a < pick(lo, k))) {
+                const int32_t lok = pick(lo, k);
+                if (lr.x >= lok) {
+                    const uint64_t n[2] = {n0, n1};
+                    const uint64_t c2s[2][2] = {{c00, c01}, {c10, c11}};
+                    const uint64_t X[2][2] = {{X00, X01}, {X10, X11}};
+                    const uint64_t Yp[2][2] = {{Y00, Y01}, {Y10, Y11}};
+                    emit_w_terms(g, D3, r, seg_end, cin_r, cin_end, lok, n, c2s, X, Yp,
                                  sacc + k * 32 * SP_COPIES);
+                }
                 k++;
             }
             if (!more) break;
@@ -1462,13 +1516,24 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
             const int64_t cin_a = g.cin[a];
             const uint64_t between_in = (uint64_t)(cin_r - (cin_a + da));
             const uint64_t between_o = (uint64_t)(r - a - 1) - between_in;
-            c2s[da][0] += n[0];
-            c2s[da][1] += n[1];
-            n[da] += 1;
-            X[da][0] += between_o;
-            X[da][1] += between_in;
-            Yp[da][0] += (uint64_t)(a - cin_a);
-            Yp[da][1] += (uint64_t)cin_a;
+            const uint64_t co_a = (uint64_t)(a - cin_a), ci_a = (uint64_t)cin_a;
+            if (da) {
+                c10 += n0;
+                c11 += n1;
+                n1 += 1;
+                X10 += between_o;
+                X11 += between_in;
+                Y10 += co_a;
+                Y11 += ci_a;
+            } else {
+                c00 += n0;
+                c01 += n1;
+                n0 += 1;
+                X00 += between_o;
+                X01 += between_in;
+                Y00 += co_a;
+                Y01 += ci_a;
+            }
             cur = a;
             a = g.lk[a].x;
         }
@@ -1480,7 +1545,7 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
         const int64_t tp = tt[p];
         const int Dp = dir_of(g.tn[p].x);
         int k = 0;
-        while (k < K && lr.x < lo[k]) k++;  // r is back-active in windows k..K-1
+        while (k < K && lr.x < pick(lo, k)) k++;  // r is back-active in windows k..K-1
         int32_t hi = k < K ? gallop_hi(tt, r, seg_end, tp, D.d[k]) : r;
         uint64_t f0 = 0, f1 = 0;
         int32_t b = r, cur = p;
@@ -1511,13 +1576,13 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
 // The Star/Pair sweep of several windows: the entries listed by
 // k_window_lo_multi, with K sets of lane copies of the 32 cells in dynamic
 // shared memory; window k's cells go to cells + 56 k.
+template <int K>
 __global__ void __launch_bounds__(THREADS)
-    k_star_pair_list_multi(const __grid_constant__ DevGraph g, const DeltaList D,
+    k_star_pair_list_multi(const __grid_constant__ DevGraph g, const __grid_constant__ DeltaList D,
                            const int32_t *__restrict__ wl, const int32_t *__restrict__ act,
                            const int32_t *__restrict__ nact_ptr, int32_t *__restrict__ head,
                            unsigned long long *__restrict__ cells) {
     extern __shared__ unsigned long long msacc[];  // [K][32 * SP_COPIES]
-    const int K = D.k;
     for (int i = threadIdx.x; i < K * 32 * SP_COPIES; i += blockDim.x) msacc[i] = 0;
     const int32_t nact = *nact_ptr;
     unsigned long long *mine = msacc + (threadIdx.x & 31);
@@ -1532,7 +1597,7 @@ __global__ void __launch_bounds__(THREADS)
         for (int j = 0; j < SP_CHUNK / THREADS; j++) {
             const int64_t i = u * SP_CHUNK + j * THREADS + threadIdx.x;
             if (i >= nact) break;
-            star_pair_back_active_multi(g, D, wl, act[i], mine);
+            star_pair_back_active_multi<K>(g, D, wl, act[i], mine);
         }
     }
     __syncthreads();
@@ -1700,6 +1765,26 @@ void launch_count(const DevGraph &g, int64_t delta, int32_t begin, int32_t end,
     }
 }
 
+// The window pass and the Star/Pair sweep of K windows.
+template <int K>
+void multi_sweep(const DevGraph &g, const DeltaList &D, const CountScratch &sc, int32_t *nact,
+                 int32_t *head, unsigned long long *dev_cells, unsigned blocks, cudaStream_t s) {
+    TM_LAUNCH(k_window_lo_multi<K>, blocks, THREADS, 0, s, g, D, sc.wl, sc.act, nact);
+    const size_t smem = sizeof(unsigned long long) * 32 * SP_COPIES * K;
+    static std::atomic<unsigned long long> attr_devices{0};
+    const int dev = current_device_id();
+    if (dev >= 64 || !((attr_devices.load() >> dev) & 1ull)) {
+        TM_CUDA(cudaFuncSetAttribute(k_star_pair_list_multi<K>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) attr_devices.fetch_or(1ull << dev);
+    }
+    int per_sm = 0;
+    TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list_multi<K>,
+                                                          THREADS, smem));
+    TM_LAUNCH(k_star_pair_list_multi<K>, (unsigned)(num_sms() * std::max(1, per_sm)), THREADS,
+              smem, s, g, D, sc.wl, sc.act, nact, head, dev_cells);
+}
+
 void launch_count_multi_delta(const DevGraph &g, const int64_t *deltas, int32_t k,
                               unsigned long long *dev_cells, cudaStream_t s) {
     const int64_t n2 = 2 * g.m;
@@ -1737,22 +1822,16 @@ void launch_count_multi_delta(const DevGraph &g, const int64_t *deltas, int32_t 
             PhaseTimer pt(TM_PH_STAR_PAIR, s);
             int64_t blocks = (n2 / COUNT_ECHUNK + WARPS_PER_BLOCK) / WARPS_PER_BLOCK;
             blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
-            TM_LAUNCH(k_window_lo_multi, (unsigned)blocks, THREADS, 0, s, g, D, sc.wl, sc.act, nact);
-            const size_t smem = sizeof(unsigned long long) * 32 * SP_COPIES * k;
-            static std::atomic<unsigned long long> attr_devices{0};
-            const int dev = current_device_id();
-            if (dev >= 64 || !((attr_devices.load() >> dev) & 1ull)) {
-                TM_CUDA(cudaFuncSetAttribute(k_star_pair_list_multi,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(unsigned long long) * 32 * SP_COPIES *
-                                                   MAX_DELTAS)));
-                if (dev < 64) attr_devices.fetch_or(1ull << dev);
+            switch (k) {
+                case 1: multi_sweep<1>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 2: multi_sweep<2>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 3: multi_sweep<3>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 4: multi_sweep<4>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 5: multi_sweep<5>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 6: multi_sweep<6>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                case 7: multi_sweep<7>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
+                default: multi_sweep<8>(g, D, sc, nact, head, dev_cells, (unsigned)blocks, s); break;
             }
-            int per_sm = 0;
-            TM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_pair_list_multi,
-                                                                  THREADS, smem));
-            TM_LAUNCH(k_star_pair_list_multi, (unsigned)(sms * std::max(1, per_sm)), THREADS, smem,
-                      s, g, D, sc.wl, sc.act, nact, head, dev_cells);
         }
         // the Tri joins of each window on its window starts, one segment at a time
         // (the graph read in place from the kernels' parameters)
