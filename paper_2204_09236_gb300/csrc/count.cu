@@ -1546,10 +1546,18 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
         const int Dp = dir_of(g.tn[p].x);
         int k = 0;
         while (k < K && lr.x < pick(lo, k)) k++;  // r is back-active in windows k..K-1
-        int32_t hi = k < K ? gallop_hi(tt, r, seg_end, tp, D.d[k]) : r;
+        // hi_j(p) of those windows, each searched from the previous one's
+        int32_t his[K];
+        int32_t h = r;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            if (j >= k) h = gallop_hi(tt, h, seg_end, tp, D.d[j]);
+            his[j] = h;
+        }
+        const int32_t hmax = his[K - 1];
+        int32_t hi = pick(his, k < K ? k : K - 1);
         uint64_t f0 = 0, f1 = 0;
         int32_t b = r, cur = p;
-        const int32_t hmax = gallop_hi(tt, r, seg_end, tp, D.d[K - 1]);
         while (k < K) {
             const bool more = b > cur && b <= hmax;  // links strictly increase: ends
             while (k < K && (!more || b > hi)) {
@@ -1562,7 +1570,7 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
                 lane_add(sk, 24 + IX(Dp, 1, 0), 0 - f1 * (uint64_t)after_o);
                 lane_add(sk, 24 + IX(Dp, 1, 1), 0 - f1 * (uint64_t)after_in);
                 k++;
-                if (k < K) hi = gallop_hi(tt, hi, seg_end, tp, D.d[k]);
+                if (k < K) hi = pick(his, k);
             }
             if (!more) break;
             if (dir_of(g.tn[b].x)) f1 += 1;
@@ -1577,7 +1585,7 @@ __device__ __forceinline__ void star_pair_back_active_multi(const DevGraph &g, c
 // k_window_lo_multi, with K sets of lane copies of the 32 cells in dynamic
 // shared memory; window k's cells go to cells + 56 k.
 template <int K>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 4)
     k_star_pair_list_multi(const __grid_constant__ DevGraph g, const __grid_constant__ DeltaList D,
                            const int32_t *__restrict__ wl, const int32_t *__restrict__ act,
                            const int32_t *__restrict__ nact_ptr, int32_t *__restrict__ head,

@@ -409,3 +409,24 @@ def test_empty_graph():
     G = oracle.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
     star, pair, tri = G.count(5)
     assert star.sum() == 0 and pair.sum() == 0 and tri.sum() == 0
+
+
+def test_fullsize_golden_files_are_complete():
+    """The stored full-size cells (written by tests/golden/make_fullsize_golden.py
+    from the oracle) cover every window of both workloads, and each stored cell
+    set satisfies the isomorphism equalities (Sec. IV-A, IV-B)."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    for name, deltas in (("large", [86400]), ("hub", [600, 3600, 86400])):
+        with open(os.path.join(here, f"fullsize_{name}.json")) as f:
+            g = json.load(f)
+        assert len(g["fingerprint"]) == 16
+        assert sorted(int(k) for k in g["counts"]) == deltas
+        for c in g["counts"].values():
+            S = np.array(c["star"], np.uint64).reshape(3, 2, 2, 2)
+            P = np.array(c["pair"], np.uint64).reshape(2, 2, 2)
+            Q = np.array(c["tri"], np.uint64).reshape(3, 2, 2, 2)
+            merged, bad = oracle.merge(S, P, Q)
+            assert bad == 0
+            assert merged.ravel().tolist() == c["classes"]
