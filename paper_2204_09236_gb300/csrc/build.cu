@@ -1,6 +1,9 @@
 // tm_build: the device-resident graph.
 //
-// Steps (one stream):
+// Steps (on the caller's stream; the entry offsets, in-prefix, link
+// initialisation and position scatter of step 4 run on a side stream beside
+// the pair sort of step 5, and the hash table is cleared beside the
+// insertion records):
 //   1. validate ids / self-loops, find n, min t, max t          (k_validate)
 //   2. stable radix sort of the edges by t - t_min -> rank order  (ties keep
 //      the edge-id order: the (t, edge id) total order); skipped when the
@@ -12,6 +15,7 @@
 //      a run of the pair list in rank order; a hash maps a pair to its run
 //   6. links between consecutive same-neighbour entries of a centre
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -402,7 +406,50 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
+// Streams of the current device for build work that runs beside s: a pool
+// of four per device, taken in turn, created on first use.
+cudaStream_t side_stream() {
+    static std::mutex mu;
+    static cudaStream_t pool[64][4] = {};
+    static std::atomic<unsigned> turn{0};
+    const int dev = current_device_id();
+    if (dev < 0 || dev >= 64) return nullptr;
+    const unsigned k = turn.fetch_add(1) & 3u;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pool[dev][k]) TM_CUDA(cudaStreamCreateWithFlags(&pool[dev][k], cudaStreamNonBlocking));
+    return pool[dev][k];
+}
+
+// Build work beside s on a side stream st: fork() lets st run after s's work
+// so far, join() makes s wait for st's work so far. The destructor joins as
+// well, so that on the way out of a failing build nothing that s frees is
+// still in use on st.
+struct Side {
+    cudaStream_t s, st;
+    cudaEvent_t ev = nullptr;
+    explicit Side(cudaStream_t s_) : s(s_) {
+        const cudaStream_t x = side_stream();
+        st = x ? x : s;
+        TM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    void fork() {
+        TM_CUDA(cudaEventRecord(ev, s));
+        TM_CUDA(cudaStreamWaitEvent(st, ev, 0));
+    }
+    void join() {
+        TM_CUDA(cudaEventRecord(ev, st));
+        TM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    }
+    ~Side() {
+        cudaEventRecord(ev, st);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    Side(const Side &) = delete;
+    Side &operator=(const Side &) = delete;
+};
+
+void build_pairs(DevGraph &g, int nb, Side &side, cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m;
     uint32_t *k1 = dev_alloc_n<uint32_t>(m, s), *k2 = dev_alloc_n<uint32_t>(m, s);
     PairPayload *v1 = dev_alloc_n<PairPayload>(m, s), *v2 = dev_alloc_n<PairPayload>(m, s);
@@ -418,11 +465,15 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
     int32_t *head = dev_alloc_n<int32_t>(m, s);
     int32_t *run_id = dev_alloc_n<int32_t>(m + 1, s);
     int32_t *cum = dev_alloc_n<int32_t>(m + 1, s);
+    side.join();  // off, cin, the links' initial value and the positions
     TM_LAUNCH(k_pair_links, grid_for(m), 256, 0, s, sk, sv, g.pos_src, g.pos_dst, m, g.pl, srcmin,
               head, g.lk);
-    exclusive_scan_i32(srcmin, cum, m, s);
-    TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, s, cum, m, g.pl);
-    dev_free(cum, s);
+    // the source-is-min prefix of the pair list beside the run ids
+    side.fork();
+    exclusive_scan_i32(srcmin, cum, m, side.st);
+    TM_LAUNCH(k_pair_cum, grid_for(m + 1), 256, 0, side.st, cum, m, g.pl);
+    dev_free(cum, side.st);
+    dev_free(srcmin, side.st);
     exclusive_scan_i32(head, run_id, m, s);
     int32_t nruns = 0;
     TM_CUDA(cudaMemcpyAsync(&nruns, run_id + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -431,7 +482,9 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
     while (cap < 2ull * (uint64_t)nruns) cap <<= 1;
     g.hash = dev_alloc_n<PairSlot>((int64_t)cap, s);
     g.hash_mask = (uint32_t)(cap - 1);
-    TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * cap, s));
+    // the table is cleared beside the insertion records
+    side.fork();
+    TM_CUDA(cudaMemsetAsync(g.hash, 0xff, sizeof(PairSlot) * cap, side.st));
     // about 8 filter bits per pair, at most 2^22 words (32 MB)
     uint64_t words = 128;
     while (words < (uint64_t)nruns / 8 && words < (1ull << 22)) words <<= 1;
@@ -456,6 +509,7 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
     radix_sort_u32_rec(rk1, rv1, rk2, rv2, nruns, bits_for((uint64_t)(nregions - 1)), s, &rks, &rvs);
     TM_LAUNCH(k_offsets, grid_for((int64_t)nruns + 1), 256, 0, s, rks, (int64_t)nruns,
               (int64_t)nregions, rstart);
+    side.join();
     for (int r = 0; r < nregions; r++)
         TM_LAUNCH(k_hash_insert, grid_for((int64_t)nruns / nregions + 1), 256, 0, s, rvs, rstart, r,
                   g.hash, g.hash_mask);
@@ -467,7 +521,6 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
     dev_free(run_begin, s);
     dev_free(run_id, s);
     dev_free(head, s);
-    dev_free(srcmin, s);
     dev_free(k1, s);
     dev_free(k2, s);
     dev_free(v1, s);
@@ -487,7 +540,7 @@ void build_pairs(DevGraph &g, int nb, cudaStream_t s) {
 template <typename K, typename Release>
 void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
                             int keybits, int nbits, bool time_ordered, Release release_inputs,
-                            cudaStream_t s) {
+                            Side &side, cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m, n = g.n;
     K *sk;
     uint64_t *sv;
@@ -549,16 +602,19 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
         dev_free(va, s);
     }
     dev_free(hist, s);
-    TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, s, reinterpret_cast<const uint32_t *>(g.tc), n2,
-              n, g.off);
-    exclusive_scan_low_bit(codes, g.cin, n2, s);
-    TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, s));
+    // the rest runs beside the pair sort, which reads only tn and tc
+    side.fork();
+    const cudaStream_t ss = side.st;
+    TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, ss, reinterpret_cast<const uint32_t *>(g.tc),
+              n2, n, g.off);
+    exclusive_scan_low_bit(codes, g.cin, n2, ss);
+    TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, ss));
     // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
     const int64_t ranks_per_pass = (int64_t)8 << 20;
     for (int64_t rlo = 0; rlo < m; rlo += ranks_per_pass)
-        TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, s, codes, n2, (uint32_t)rlo,
+        TM_LAUNCH(k_pos_scatter, grid_for(n2), 256, 0, ss, codes, n2, (uint32_t)rlo,
                   (uint32_t)std::min<int64_t>(m, rlo + ranks_per_pass), g.pos_src, g.pos_dst);
-    dev_free(codes, s);
+    dev_free(codes, ss);
 }
 
 }  // namespace
@@ -684,18 +740,20 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     const int keybits = bits_for(span);
     const int nbits = bits_for((uint64_t)(n - 1));
     const bool time_ordered = hv.unsorted == 0;
+    Side side(s);
     if (keybits <= 32)
         sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, time_ordered,
-                                         release_inputs, s);
+                                         release_inputs, side, s);
     else
         sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, time_ordered,
-                                         release_inputs, s);
+                                         release_inputs, side, s);
 
     // 5-6. pair list, same-neighbour links, hash
     {
         PhaseTimer pt(TM_PH_PAIRS, s);
-        build_pairs(g, nbits, s);
+        build_pairs(g, nbits, side, s);
     }
+    side.join();
     TM_CUDA(cudaStreamSynchronize(s));
 }
 
