@@ -89,6 +89,24 @@ __global__ void k_time_keys(const int32_t *__restrict__ src, const int32_t *__re
     }
 }
 
+// The first pass of the time sort forms its items from the edges in id
+// order: key t - t_min, value (src << 32) | dst.
+template <typename K>
+struct TimeGen {
+    static constexpr bool VEC_KEYS = false;
+    const int32_t *__restrict__ src;
+    const int32_t *__restrict__ dst;
+    const int64_t *__restrict__ t;
+    long long tmin;
+    __device__ __forceinline__ bool valid(int64_t) const { return true; }
+    __device__ __forceinline__ K key(int64_t e) const {
+        return (K)((unsigned long long)t[e] - (unsigned long long)tmin);
+    }
+    __device__ __forceinline__ uint64_t val(int64_t e) const {
+        return ((uint64_t)(uint32_t)src[e] << 32) | (uint32_t)dst[e];
+    }
+};
+
 // The incident entries, generated from the edges in rank order as the first
 // pass of their sort by centre reads them: entry i = 2 * rank + side of the
 // edge of that rank sits at its source (side 0, direction o) or destination
@@ -548,23 +566,27 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     uint64_t *v1 = dev_alloc_n<uint64_t>(m, s);
     {
         PhaseTimer pt(TM_PH_TIME_SORT, s);
-        TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin, k1,
-                  v1);
-        release_inputs();
         if (time_ordered) {
+            TM_LAUNCH(k_time_keys<K>, grid_for(m), 256, 0, s, src, dst, t, m, (long long)g.tmin,
+                      k1, v1);
             sk = k1;
             sv = v1;
         } else {
+            // the first pass reads the edge arrays themselves; the last writes
+            // the pair it does not read (see radix::sort)
             K *k2 = dev_alloc_n<K>(m, s);
             uint64_t *v2 = dev_alloc_n<uint64_t>(m, s);
-            if constexpr (sizeof(K) == 4)
-                radix_sort_u32_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
-            else
-                radix_sort_u64_v64(k1, v1, k2, v2, m, keybits, s, &sk, &sv);
+            const int passes = keybits > 8 ? (keybits + 7) / 8 : 1;
+            sk = passes & 1 ? k1 : k2;
+            sv = passes & 1 ? v1 : v2;
+            radix::sort<K, uint64_t>(TimeGen<K>{src, dst, t, (long long)g.tmin},
+                                     radix::ArrayOut<K, uint64_t>{sk, sv}, k1, v1, k2, v2, m, m,
+                                     keybits, s);
             // the pair not holding the result is free now
             dev_free(sk == k1 ? k2 : k1, s);
             dev_free(sv == v1 ? v2 : v1, s);
         }
+        release_inputs();
     }
     PhaseTimer pt(TM_PH_INCIDENT, s);
     uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);

@@ -152,13 +152,6 @@ void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
                                            vals_out);
 }
 
-void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
-                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
-                        uint64_t **vals_out) {
-    radix_sort_impl<uint32_t, uint64_t>(keys, vals, keys_tmp, vals_tmp, n, bits, s, keys_out,
-                                        vals_out);
-}
-
 void radix_sort_u64_v64(uint64_t *keys, uint64_t *vals, uint64_t *keys_tmp, uint64_t *vals_tmp,
                         int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
                         uint64_t **vals_out) {

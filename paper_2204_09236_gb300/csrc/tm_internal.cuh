@@ -178,9 +178,6 @@ void radix_sort_u32_rec(uint32_t *keys, HashRecord *vals, uint32_t *keys_tmp, Ha
 void radix_sort_u32_pair(uint32_t *keys, PairPayload *vals, uint32_t *keys_tmp,
                          PairPayload *vals_tmp, int64_t n, int bits, cudaStream_t s,
                          uint32_t **keys_out, PairPayload **vals_out);
-void radix_sort_u32_v64(uint32_t *keys, uint64_t *vals, uint32_t *keys_tmp, uint64_t *vals_tmp,
-                        int64_t n, int bits, cudaStream_t s, uint32_t **keys_out,
-                        uint64_t **vals_out);
 void radix_sort_u64_v64(uint64_t *keys, uint64_t *vals, uint64_t *keys_tmp, uint64_t *vals_tmp,
                         int64_t n, int bits, cudaStream_t s, uint64_t **keys_out,
                         uint64_t **vals_out);
