@@ -228,8 +228,19 @@ __global__ void k_pos_scatter(const uint32_t *__restrict__ codes, int64_t n2, ui
 // Consecutive edges of one node pair are consecutive same-neighbour entries at
 // both of its nodes. Entries whose pair has one edge keep the links of the
 // memset (-1, -1); the others get their whole (prev, next) from their own
-// element. A warp takes 32 consecutive elements and passes the neighbouring
-// elements' keys and entry positions along with shuffles.
+// element. A warp takes LINK_U groups of 32 consecutive elements at a time
+// (the random position reads of all groups in flight together) and passes the
+// neighbouring elements' keys and entry positions along with shuffles, across
+// group borders too; only the elements just outside its 32 * LINK_U are read
+// again.
+constexpr int LINK_U = 4;
+
+__device__ __forceinline__ int32_t big_pos(const PairPayload &q, const int32_t *__restrict__ pos_src,
+                                           const int32_t *__restrict__ pos_dst) {
+    // entry position at the larger endpoint
+    return q.srcmin() ? pos_dst[q.rank] : pos_src[q.rank];
+}
+
 __global__ void k_pair_links(const uint32_t *__restrict__ pkey, const PairPayload *__restrict__ pp,
                              const int32_t *__restrict__ pos_src,
                              const int32_t *__restrict__ pos_dst, int64_t m, int2 *__restrict__ pl,
@@ -237,59 +248,90 @@ __global__ void k_pair_links(const uint32_t *__restrict__ pkey, const PairPayloa
                              int2 *__restrict__ lk) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5 << 5; base < m;
-         base += nwarps * 32) {
-        const int64_t k = base + lane;
-        const bool in = k < m;
-        PairPayload q{};
-        uint32_t key = 0xffffffffu;
-        if (in) {
-            q = pp[k];
-            key = pkey[k];
-        }
-        // the neighbouring elements: shuffles inside the warp, loads across its edges
-        uint32_t key_p = __shfl_up_sync(0xffffffffu, key, 1);
-        uint32_t cen_p = __shfl_up_sync(0xffffffffu, q.centre, 1);
-        uint32_t key_n = __shfl_down_sync(0xffffffffu, key, 1);
-        uint32_t cen_n = __shfl_down_sync(0xffffffffu, q.centre, 1);
-        PairPayload qp{}, qn{};
-        if (in && lane == 0 && k > 0) {
-            qp = pp[k - 1];
-            key_p = pkey[k - 1];
-            cen_p = qp.centre;
-        }
-        if (in && (lane == 31 || k + 1 == m)) {
-            key_n = 0xffffffffu;
-            if (k + 1 < m) {
-                qn = pp[k + 1];
-                key_n = pkey[k + 1];
-                cen_n = qn.centre;
+    constexpr unsigned FULL = 0xffffffffu;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 * LINK_U);
+         base < m; base += nwarps * (32 * LINK_U)) {
+        PairPayload q[LINK_U];
+        uint32_t key[LINK_U];
+#pragma unroll
+        for (int u = 0; u < LINK_U; u++) {
+            const int64_t k = base + 32 * u + lane;
+            q[u] = PairPayload{};
+            key[u] = 0xffffffffu;
+            if (k < m) {
+                q[u] = pp[k];
+                key[u] = pkey[k];
             }
         }
-        const bool same_p = in && k > 0 && key_p == key && cen_p == q.centre;
-        const bool same_n = in && k + 1 < m && key_n == key && cen_n == q.centre;
-        // entry position at the larger endpoint, for elements with a neighbour
-        int32_t big = -1;
-        if (same_p || same_n) big = q.srcmin() ? pos_dst[q.rank] : pos_src[q.rank];
-        int32_t pos_p = __shfl_up_sync(0xffffffffu, (int32_t)q.pos(), 1);
-        int32_t big_p = __shfl_up_sync(0xffffffffu, big, 1);
-        int32_t pos_n = __shfl_down_sync(0xffffffffu, (int32_t)q.pos(), 1);
-        int32_t big_n = __shfl_down_sync(0xffffffffu, big, 1);
-        if (!in) continue;
-        if (lane == 0 && same_p) {
-            pos_p = (int32_t)qp.pos();
-            big_p = qp.srcmin() ? pos_dst[qp.rank] : pos_src[qp.rank];
+        // the elements just before and after the warp's range
+        PairPayload qp{}, qn{};
+        uint32_t kp = 0xffffffffu, kn = 0xffffffffu;
+        if (lane == 0 && base > 0 && base - 1 < m) {
+            qp = pp[base - 1];
+            kp = pkey[base - 1];
         }
-        if (lane == 31 && same_n) {
-            pos_n = (int32_t)qn.pos();
-            big_n = qn.srcmin() ? pos_dst[qn.rank] : pos_src[qn.rank];
+        const int64_t after = base + 32 * LINK_U;
+        if (lane == 31 && after < m) {
+            qn = pp[after];
+            kn = pkey[after];
         }
-        pl[k].x = q.rank;
-        srcmin[k] = (int32_t)q.srcmin();
-        head[k] = same_p ? 0 : 1;
-        if (same_p || same_n) {
-            lk[q.pos()] = make_int2(same_p ? pos_p : -1, same_n ? pos_n : -1);
-            lk[big] = make_int2(same_p ? big_p : -1, same_n ? big_n : -1);
+        bool same_p[LINK_U], same_n[LINK_U];
+        int32_t big[LINK_U];
+#pragma unroll
+        for (int u = 0; u < LINK_U; u++) {
+            const int64_t k = base + 32 * u + lane;
+            uint32_t key_p = __shfl_up_sync(FULL, key[u], 1);
+            uint32_t cen_p = __shfl_up_sync(FULL, q[u].centre, 1);
+            uint32_t key_n = __shfl_down_sync(FULL, key[u], 1);
+            uint32_t cen_n = __shfl_down_sync(FULL, q[u].centre, 1);
+            // across the group borders: lane 31 of the group before, lane 0 of the one after
+            const uint32_t kb = __shfl_sync(FULL, key[u > 0 ? u - 1 : 0], 31);
+            const uint32_t cb = __shfl_sync(FULL, q[u > 0 ? u - 1 : 0].centre, 31);
+            const uint32_t ka = __shfl_sync(FULL, key[u + 1 < LINK_U ? u + 1 : u], 0);
+            const uint32_t ca = __shfl_sync(FULL, q[u + 1 < LINK_U ? u + 1 : u].centre, 0);
+            if (lane == 0) {
+                key_p = u > 0 ? kb : kp;
+                cen_p = u > 0 ? cb : qp.centre;
+            }
+            if (lane == 31) {
+                key_n = u + 1 < LINK_U ? ka : kn;
+                cen_n = u + 1 < LINK_U ? ca : qn.centre;
+            }
+            const bool in = k < m;
+            same_p[u] = in && k > 0 && key_p == key[u] && cen_p == q[u].centre;
+            same_n[u] = in && k + 1 < m && key_n == key[u] && cen_n == q[u].centre;
+            big[u] = (same_p[u] || same_n[u]) ? big_pos(q[u], pos_src, pos_dst) : -1;
+        }
+        int32_t big_before = -1, big_after = -1;
+        if (lane == 0 && same_p[0]) big_before = big_pos(qp, pos_src, pos_dst);
+        if (lane == 31 && same_n[LINK_U - 1]) big_after = big_pos(qn, pos_src, pos_dst);
+#pragma unroll
+        for (int u = 0; u < LINK_U; u++) {
+            const int64_t k = base + 32 * u + lane;
+            int32_t pos_p = __shfl_up_sync(FULL, (int32_t)q[u].pos(), 1);
+            int32_t big_p = __shfl_up_sync(FULL, big[u], 1);
+            int32_t pos_n = __shfl_down_sync(FULL, (int32_t)q[u].pos(), 1);
+            int32_t big_n = __shfl_down_sync(FULL, big[u], 1);
+            const int32_t pb = __shfl_sync(FULL, (int32_t)q[u > 0 ? u - 1 : 0].pos(), 31);
+            const int32_t bb = __shfl_sync(FULL, big[u > 0 ? u - 1 : 0], 31);
+            const int32_t pa = __shfl_sync(FULL, (int32_t)q[u + 1 < LINK_U ? u + 1 : u].pos(), 0);
+            const int32_t ba = __shfl_sync(FULL, big[u + 1 < LINK_U ? u + 1 : u], 0);
+            if (lane == 0) {
+                pos_p = u > 0 ? pb : (int32_t)qp.pos();
+                big_p = u > 0 ? bb : big_before;
+            }
+            if (lane == 31) {
+                pos_n = u + 1 < LINK_U ? pa : (int32_t)qn.pos();
+                big_n = u + 1 < LINK_U ? ba : big_after;
+            }
+            if (k >= m) continue;
+            pl[k].x = q[u].rank;
+            srcmin[k] = (int32_t)q[u].srcmin();
+            head[k] = same_p[u] ? 0 : 1;
+            if (same_p[u] || same_n[u]) {
+                lk[q[u].pos()] = make_int2(same_p[u] ? pos_p : -1, same_n[u] ? pos_n : -1);
+                lk[big[u]] = make_int2(same_p[u] ? big_p : -1, same_n[u] ? big_n : -1);
+            }
         }
     }
 }
