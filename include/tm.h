@@ -64,8 +64,11 @@ tm_graph *tm_build(const int32_t *src, const int32_t *dst, const int64_t *t, int
 
 /* Same as tm_build, enqueued on `stream` (a cudaStream_t; NULL = legacy
  * default stream). Device inputs must be ready in stream order. The call
- * still waits for one small device-to-host read (node count, timestamp
- * range, validation flags) before it sizes the graph's buffers. */
+ * waits for two small device-to-host reads (node count, timestamp range and
+ * validation flags, which size the graph's buffers; the number of node pairs,
+ * which sizes the hash) and returns once the build's work has finished. Part
+ * of that work runs on internal side streams forked from `stream` and joined
+ * back into it. */
 tm_graph *tm_build_async(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t m,
                          void *stream);
 
