@@ -728,12 +728,22 @@ struct PairCounts {
     int32_t nb, na, fb, fa;
 };
 
-// L2 eviction policy "keep": the Bloom filter is read by every probe.
-__device__ __forceinline__ uint64_t load_keep(const uint64_t *p) {
-    uint64_t v, pol;
+// L2 eviction policy "keep": the Bloom filter is read by every probe. The
+// policy is created once per call of a probe loop and passed to its loads.
+__device__ __forceinline__ uint64_t keep_policy() {
+    uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint64_t load_keep_pol(const uint64_t *p, uint64_t pol) {
+    uint64_t v;
     asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
     return v;
+}
+
+__device__ __forceinline__ uint64_t load_keep(const uint64_t *p) {
+    return load_keep_pol(p, keep_policy());
 }
 
 // As pair_counts, for a pair that passed the Bloom filter.
@@ -957,6 +967,7 @@ __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEd
                                                   TriProbe *q, int &qn,
                                                   unsigned long long (&acc)[8]) {
     const int lane = threadIdx.x & 31;
+    const uint64_t pol = keep_policy();
     int last[2] = {0, 0};
     for (int32_t jb = 0; jb < total; jb += 64) {
         int32_t j[2], own[2];
@@ -1004,7 +1015,7 @@ __device__ __forceinline__ void tri_probes_queued(const DevGraph &g, const TriEd
             key[k] = pair_key(big, x);
             uint32_t word;
             bits[k] = bloom_bits(key[k], g.bloom_mask, &word);
-            bw[k] = cand[k] ? load_keep(g.bloom + word) : 0;
+            bw[k] = cand[k] ? load_keep_pol(g.bloom + word, pol) : 0;
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
