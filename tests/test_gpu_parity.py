@@ -162,6 +162,16 @@ def test_extreme_timestamps(tm):
     assert_parity(tm, s, d, t, [0, 2 ** 58, 2 ** 60, 2 ** 63 - 1])
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_wide_time_span_multi_tile(tm, seed):
+    """Timestamps spanning 42 bits over many sort tiles: the 64-bit time keys
+    (six passes, the first forming its items from the edge arrays) and the
+    20-byte entry payloads. Times are multiples of 2^30, so ties survive."""
+    s, d, t = synth.random_small(700 + seed, 80, 20000 + 3001 * seed, 1 << 12)
+    t = t * (1 << 30) + (1 << 40)
+    assert_parity(tm, s, d, t, [0, 1 << 30, 5 << 30, 60 << 30])
+
+
 def test_sparse_node_ids(tm):
     s, d, t = synth.random_small(8, 8, 200, 40)
     ids = np.array([0, 17, 4095, 70000, 123457, 999999, 3000000, 5000000], np.int32)
