@@ -634,9 +634,6 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);
     // a 32-bit time key travels as a 32-bit timestamp
     using V = std::conditional_t<sizeof(K) == 4, EntryPayload32, EntryPayload>;
-    // the rank-ordered (src, dst) words stay with the graph: the Tri job pass
-    // walks the edges in rank order
-    g.sd = sv;
     using radix::ArrayIn;
     using radix::ArrayOut;
     const EntryGen<K, V> gen{sk, sv};
@@ -647,11 +644,13 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     if (passes == 1) {
         radix::pass<uint32_t, V>(gen, out, n2, 0, hist, s);
         dev_free(sk, s);
+        dev_free(sv, s);
     } else {
         uint32_t *ka = dev_alloc_n<uint32_t>(n2, s);
         V *va = dev_alloc_n<V>(n2, s);
         radix::pass<uint32_t, V>(gen, ArrayOut<uint32_t, V>{ka, va}, n2, 0, hist, s);
         dev_free(sk, s);
+        dev_free(sv, s);
         for (int p = 1; p + 1 < passes; p++) {
             uint32_t *kb = dev_alloc_n<uint32_t>(n2, s);
             V *vb = dev_alloc_n<V>(n2, s);
@@ -693,7 +692,6 @@ void free_graph(DevGraph &g, cudaStream_t s) {
     dev_free(g.off, s);
     dev_free(g.pos_src, s);
     dev_free(g.pos_dst, s);
-    dev_free(g.sd, s);
     dev_free(g.pl, s);
     dev_free(g.hash, s);
     dev_free(g.bloom, s);

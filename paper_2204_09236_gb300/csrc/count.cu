@@ -1165,71 +1165,6 @@ __device__ __forceinline__ void tri_jobs_step(const SegArgs &A, const DevGraph &
     }
 }
 
-// As tri_jobs_step, over the 32 * JOB_U edges of ranks from base (below m)
-// of a whole graph: an edge's two entries come from the position arrays and
-// its endpoints from the rank-ordered (src, dst) words, all read coalesced;
-// the window starts of its two entries are then random reads, but within the
-// thin band of every centre's entries around the edge's time, which the
-// warps of the grid sweep together (rank order is time order).
-template <bool SHARD>
-__device__ __forceinline__ void tri_jobs_step_ranks(const SegArgs &A, const DevGraph &g,
-                                                    const int32_t *__restrict__ swl, int64_t base,
-                                                    int64_t m, TriEdge *wb, int &cnt,
-                                                    TriEdge *__restrict__ jobs,
-                                                    int32_t *__restrict__ njobs) {
-    const int lane = threadIdx.x & 31;
-    int32_t r[JOB_U], tw[JOB_U], lo_u[JOB_U], lo_w[JOB_U];
-    uint64_t uw[JOB_U];
-#pragma unroll
-    for (int k = 0; k < JOB_U; k++) {
-        const int64_t j = base + k * 32 + lane;
-        r[k] = tw[k] = 0;
-        uw[k] = 0;
-        if (j < m) {
-            r[k] = g.pos_src[j];
-            tw[k] = g.pos_dst[j];
-            uw[k] = g.sd[j];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < JOB_U; k++) {
-        const int64_t j = base + k * 32 + lane;
-        lo_u[k] = r[k];
-        lo_w[k] = tw[k];
-        if (j < m) {
-            lo_u[k] = swl[r[k]];
-            lo_w[k] = swl[tw[k]];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < JOB_U; k++) {
-        const int64_t j = base + k * 32 + lane;
-        bool has = j < m && lo_u[k] < r[k] && lo_w[k] < tw[k];
-        TriEdge E;
-        if (has) {
-            const uint32_t u = (uint32_t)(uw[k] >> 32), w = (uint32_t)uw[k];
-            E = make_tri_edge(g, r[k], u, w, (int32_t)j, lo_u[k], tw[k], lo_w[k]);
-            if (SHARD) {
-                const bool cu = owns(A, u), cw = owns(A, w);
-                has = cu || cw;
-                E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
-            }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, has);
-        if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
-        cnt += __popc(bal);
-    }
-    __syncwarp();
-    while (cnt >= 32) {
-        int32_t first = 0;
-        if (lane == 0) first = atomicAdd(njobs, 32);
-        first = __shfl_sync(0xffffffffu, first, 0);
-        jobs[first + lane] = wb[cnt - 32 + lane];
-        cnt -= 32;
-        __syncwarp();
-    }
-}
-
 // The warp's last cnt (< 32) buffered joins appended to jobs.
 __device__ __forceinline__ void tri_jobs_flush(const TriEdge *wb, int cnt,
                                                TriEdge *__restrict__ jobs,
@@ -1253,16 +1188,10 @@ __device__ __forceinline__ void tri_jobs_flush(const TriEdge *wb, int cnt,
 // ones, and the chain of dependent reads that finds a join is paid here, in
 // a kernel that does nothing else. A warp gathers its jobs in shared memory
 // and reserves space 32 at a time, so the shared counter takes one atomic per
-// 32 jobs. On a whole graph the warps sweep the edges in rank order, steps of
-// 32 * JOB_U ranks strided over the grid: rank order is time order, so at any
-// moment the grid's random reads (window starts, the big window's first
-// rank) fall in a thin time band of every centre's entries, which L2 holds,
-// where an entry-order sweep scatters them over all times (on the hub-skewed
-// graph this takes the Tri phase from 0.41 to 0.34 ms at delta = 3600 and
-// from 3.34 to 3.02 ms at 86400 on 15M edges). On a part of a graph the warps
-// sweep steps of entries, and they flush once at the end; on a table a warp
-// takes units of echunk entries of one segment and flushes at the end of each
-// unit.
+// 32 jobs. On one graph the warps sweep steps of 32 * JOB_U entries strided
+// over the grid (all warps together stream one region of the arrays) and
+// flush once at the end; on a table a warp takes units of echunk entries of
+// one segment and flushes at the end of each unit.
 template <bool ONE, bool SHARD>
 __global__ void __launch_bounds__(THREADS)
     k_tri_jobs(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
@@ -1277,15 +1206,9 @@ __global__ void __launch_bounds__(THREADS)
         const Segment &sg = A.seg0;
         const int32_t *__restrict__ swl = wl + (sg.xbase - sg.begin);  // swl[r] = wl[x(r)]
         TriEdge *sjobs = jobs + sg.xbase / 2;
-        if (sg.begin == 0 && (int64_t)sg.end == 2 * sg.g.m) {
-            // a whole graph: its edges in rank order
-            for (int64_t base = wid * (32 * JOB_U); base < sg.g.m; base += nwarps * (32 * JOB_U))
-                tri_jobs_step_ranks<SHARD>(A, sg.g, swl, base, sg.g.m, wb, cnt, sjobs, njobs);
-        } else {
-            for (int64_t base = sg.begin + wid * (32 * JOB_U); base < sg.end;
-                 base += nwarps * (32 * JOB_U))
-                tri_jobs_step<SHARD>(A, sg.g, swl, base, sg.end, wb, cnt, sjobs, njobs);
-        }
+        for (int64_t base = sg.begin + wid * (32 * JOB_U); base < sg.end;
+             base += nwarps * (32 * JOB_U))
+            tri_jobs_step<SHARD>(A, sg.g, swl, base, sg.end, wb, cnt, sjobs, njobs);
         tri_jobs_flush(wb, cnt, sjobs, njobs);
     } else {
         const int64_t nu = seg_units<ONE>(A);

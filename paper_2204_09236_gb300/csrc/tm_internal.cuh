@@ -78,8 +78,7 @@ constexpr uint64_t EMPTY_KEY = ~0ull;
 // The incident sequences S_u (Table 1: e = (t, v, dir) w.r.t. centre u) of
 // all centres, one after the other, each in (t, edge id) order; entry p of
 // the whole sequence is spread over the arrays below (structure of arrays,
-// 32 bytes per entry, plus 16 bytes per edge by rank), so that every kernel
-// reads only the fields it needs.
+// 32 bytes per entry), so that every kernel reads only the fields it needs.
 struct DevGraph {
     int64_t m = 0;
     int32_t n = 0;
@@ -93,7 +92,6 @@ struct DevGraph {
     int32_t *off = nullptr;     // n+1: S_u = entries [off[u], off[u+1])
     int32_t *pos_src = nullptr; // m, by rank: entry of the edge at its source
     int32_t *pos_dst = nullptr; // m, by rank: entry of the edge at its destination
-    uint64_t *sd = nullptr;     // m, by rank: (source << 32) | destination
     // pair list, m+1 entries: runs = E_(v,w) (grouped by node pair, ranks
     // ascending); .x = rank of the edge, .y = exclusive prefix over the list of
     // "source is the smaller id" (entry m holds the total).
