@@ -177,6 +177,19 @@ __global__ void k_offsets(const uint32_t *__restrict__ centre, int64_t n2, int64
     }
 }
 
+// Entries at the centres of degree >= dmin, summed into *sum (few centres
+// pass, so few atomics).
+__global__ void k_heavy_entries(const int32_t *__restrict__ off, int64_t n, int64_t dmin,
+                                unsigned long long *__restrict__ sum) {
+    unsigned long long local = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = (int64_t)off[u + 1] - off[u];
+        if (d >= dmin) local += (unsigned long long)d;
+    }
+    if (local) atomicAdd(sum, local);
+}
+
 // pos_src / pos_dst[rank] = position of the edge's entry at its source /
 // destination, for the ranks in [rlo, rhi) only. The build runs this once per
 // rank range whose part of the two arrays fits in L2, so the random 4-byte
@@ -500,9 +513,13 @@ struct Side {
         TM_CUDA(cudaEventRecord(ev, st));
         TM_CUDA(cudaStreamWaitEvent(s, ev, 0));
     }
-    ~Side() {
+    // join() without error checks, for the way out of a failing build
+    void join_quiet() {
         cudaEventRecord(ev, st);
         cudaStreamWaitEvent(s, ev, 0);
+    }
+    ~Side() {
+        join_quiet();
         cudaEventDestroy(ev);
     }
     Side(const Side &) = delete;
@@ -600,7 +617,8 @@ void build_pairs(DevGraph &g, int nb, Side &side, cudaStream_t s) {
 template <typename K, typename Release>
 void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_t *t, DevGraph &g,
                             int keybits, int nbits, bool time_ordered, Release release_inputs,
-                            Side &side, cudaStream_t s) {
+                            Side &side, uint64_t **rank_sd, unsigned long long *heavy,
+                            cudaStream_t s) {
     const int64_t m = g.m, n2 = 2 * m, n = g.n;
     K *sk;
     uint64_t *sv;
@@ -630,6 +648,7 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
         }
         release_inputs();
     }
+    *rank_sd = sv;  // the rank-ordered (src, dst) words: the caller keeps or frees them
     PhaseTimer pt(TM_PH_INCIDENT, s);
     uint32_t *codes = dev_alloc_n<uint32_t>(n2, s);
     // a 32-bit time key travels as a 32-bit timestamp
@@ -644,13 +663,11 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     if (passes == 1) {
         radix::pass<uint32_t, V>(gen, out, n2, 0, hist, s);
         dev_free(sk, s);
-        dev_free(sv, s);
     } else {
         uint32_t *ka = dev_alloc_n<uint32_t>(n2, s);
         V *va = dev_alloc_n<V>(n2, s);
         radix::pass<uint32_t, V>(gen, ArrayOut<uint32_t, V>{ka, va}, n2, 0, hist, s);
         dev_free(sk, s);
-        dev_free(sv, s);
         for (int p = 1; p + 1 < passes; p++) {
             uint32_t *kb = dev_alloc_n<uint32_t>(n2, s);
             V *vb = dev_alloc_n<V>(n2, s);
@@ -671,6 +688,9 @@ void sort_edges_and_entries(const int32_t *src, const int32_t *dst, const int64_
     const cudaStream_t ss = side.st;
     TM_LAUNCH(k_offsets, grid_for(n2 + 1), 256, 0, ss, reinterpret_cast<const uint32_t *>(g.tc),
               n2, n, g.off);
+    // how concentrated the entries are: those at centres holding 1/64 of them or more
+    TM_LAUNCH(k_heavy_entries, grid_for(n), 256, 0, ss, g.off, n, std::max<int64_t>(1, n2 / 64),
+              heavy);
     exclusive_scan_low_bit(codes, g.cin, n2, ss);
     TM_CUDA(cudaMemsetAsync(g.lk, 0xff, sizeof(int2) * n2, ss));
     // both position arrays take 8 bytes per rank: at most 64 MB of them per pass
@@ -692,6 +712,7 @@ void free_graph(DevGraph &g, cudaStream_t s) {
     dev_free(g.off, s);
     dev_free(g.pos_src, s);
     dev_free(g.pos_dst, s);
+    dev_free(g.sd, s);
     dev_free(g.pl, s);
     dev_free(g.hash, s);
     dev_free(g.bloom, s);
@@ -805,20 +826,37 @@ void build_graph(const int32_t *src_in, const int32_t *dst_in, const int64_t *t_
     const int nbits = bits_for((uint64_t)(n - 1));
     const bool time_ordered = hv.unsorted == 0;
     Side side(s);
-    if (keybits <= 32)
-        sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, time_ordered,
-                                         release_inputs, side, s);
-    else
-        sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, time_ordered,
-                                         release_inputs, side, s);
+    uint64_t *rank_sd = nullptr;
+    unsigned long long *heavy = dev_alloc_n<unsigned long long>(1, s);
+    TM_CUDA(cudaMemsetAsync(heavy, 0, sizeof(unsigned long long), s));
+    try {
+        if (keybits <= 32)
+            sort_edges_and_entries<uint32_t>(src, dst, t, g, keybits, nbits, time_ordered,
+                                             release_inputs, side, &rank_sd, heavy, s);
+        else
+            sort_edges_and_entries<uint64_t>(src, dst, t, g, keybits, nbits, time_ordered,
+                                             release_inputs, side, &rank_sd, heavy, s);
 
-    // 5-6. pair list, same-neighbour links, hash
-    {
-        PhaseTimer pt(TM_PH_PAIRS, s);
-        build_pairs(g, nbits, side, s);
+        // 5-6. pair list, same-neighbour links, hash
+        {
+            PhaseTimer pt(TM_PH_PAIRS, s);
+            build_pairs(g, nbits, side, s);
+        }
+    } catch (...) {
+        side.join_quiet();
+        dev_free(rank_sd, s);
+        dev_free(heavy, s);
+        throw;
     }
     side.join();
+    unsigned long long hh = 0;
+    TM_CUDA(cudaMemcpyAsync(&hh, heavy, sizeof hh, cudaMemcpyDeviceToHost, s));
+    dev_free(heavy, s);
     TM_CUDA(cudaStreamSynchronize(s));
+    // a graph with 15 % or more of its entries at such centres keeps its
+    // rank-ordered endpoints, and its Tri jobs are found in rank order
+    if (20 * hh >= 3 * (unsigned long long)(2 * m)) g.sd = rank_sd;
+    else dev_free(rank_sd, s);
 }
 
 }  // namespace tmi

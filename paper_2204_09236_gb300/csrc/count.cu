@@ -1165,6 +1165,71 @@ __device__ __forceinline__ void tri_jobs_step(const SegArgs &A, const DevGraph &
     }
 }
 
+// As tri_jobs_step, over the 32 * JOB_U edges of ranks from base (below m)
+// of a whole graph: an edge's two entries come from the position arrays and
+// its endpoints from the rank-ordered (src, dst) words, all read coalesced;
+// the window starts of its two entries are then random reads, but within the
+// thin band of every centre's entries around the edge's time, which the
+// warps of the grid sweep together (rank order is time order).
+template <bool SHARD>
+__device__ __forceinline__ void tri_jobs_step_ranks(const SegArgs &A, const DevGraph &g,
+                                                    const int32_t *__restrict__ swl, int64_t base,
+                                                    int64_t m, TriEdge *wb, int &cnt,
+                                                    TriEdge *__restrict__ jobs,
+                                                    int32_t *__restrict__ njobs) {
+    const int lane = threadIdx.x & 31;
+    int32_t r[JOB_U], tw[JOB_U], lo_u[JOB_U], lo_w[JOB_U];
+    uint64_t uw[JOB_U];
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t j = base + k * 32 + lane;
+        r[k] = tw[k] = 0;
+        uw[k] = 0;
+        if (j < m) {
+            r[k] = g.pos_src[j];
+            tw[k] = g.pos_dst[j];
+            uw[k] = g.sd[j];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t j = base + k * 32 + lane;
+        lo_u[k] = r[k];
+        lo_w[k] = tw[k];
+        if (j < m) {
+            lo_u[k] = swl[r[k]];
+            lo_w[k] = swl[tw[k]];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < JOB_U; k++) {
+        const int64_t j = base + k * 32 + lane;
+        bool has = j < m && lo_u[k] < r[k] && lo_w[k] < tw[k];
+        TriEdge E;
+        if (has) {
+            const uint32_t u = (uint32_t)(uw[k] >> 32), w = (uint32_t)uw[k];
+            E = make_tri_edge(g, r[k], u, w, (int32_t)j, lo_u[k], tw[k], lo_w[k]);
+            if (SHARD) {
+                const bool cu = owns(A, u), cw = owns(A, w);
+                has = cu || cw;
+                E.rank_lo_big |= (cu ? 0 : 0x40000000) | (cw ? 0 : (int32_t)0x80000000);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        if (has) wb[cnt + __popc(bal & ((1u << lane) - 1u))] = E;
+        cnt += __popc(bal);
+    }
+    __syncwarp();
+    while (cnt >= 32) {
+        int32_t first = 0;
+        if (lane == 0) first = atomicAdd(njobs, 32);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        jobs[first + lane] = wb[cnt - 32 + lane];
+        cnt -= 32;
+        __syncwarp();
+    }
+}
+
 // The warp's last cnt (< 32) buffered joins appended to jobs.
 __device__ __forceinline__ void tri_jobs_flush(const TriEdge *wb, int cnt,
                                                TriEdge *__restrict__ jobs,
@@ -1189,9 +1254,11 @@ __device__ __forceinline__ void tri_jobs_flush(const TriEdge *wb, int cnt,
 // a kernel that does nothing else. A warp gathers its jobs in shared memory
 // and reserves space 32 at a time, so the shared counter takes one atomic per
 // 32 jobs. On one graph the warps sweep steps of 32 * JOB_U entries strided
-// over the grid (all warps together stream one region of the arrays) and
-// flush once at the end; on a table a warp takes units of echunk entries of
-// one segment and flushes at the end of each unit.
+// over the grid (all warps together stream one region of the arrays, and an
+// empty source window is seen in a coalesced read) and flush once at the
+// end; on a table a warp takes units of echunk entries of one segment and
+// flushes at the end of each unit. k_tri_jobs_ranks is the sweep in rank
+// order for a whole graph whose entries are concentrated on few nodes.
 template <bool ONE, bool SHARD>
 __global__ void __launch_bounds__(THREADS)
     k_tri_jobs(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
@@ -1226,6 +1293,32 @@ __global__ void __launch_bounds__(THREADS)
             cnt = 0;
         }
     }
+}
+
+// k_tri_jobs for a whole graph (segment [0, 2m)) that kept its rank-ordered
+// endpoints (g.sd: the build keeps them when 15 % or more of the entries sit
+// at centres holding 1/64 of them each): the edges are swept in rank order,
+// which is time order, so at any moment the grid's random reads (the window
+// starts, the big window's first rank) fall in one thin time band of every
+// centre, which L2 holds; an entry-order sweep over a hub's long segment
+// scatters them over all of its times. A kernel of its own, so that the
+// entry-order sweep keeps its registers and occupancy.
+template <bool SHARD>
+__global__ void __launch_bounds__(THREADS)
+    k_tri_jobs_ranks(const __grid_constant__ SegArgs A, const int32_t *__restrict__ wl,
+                     TriEdge *__restrict__ jobs, int32_t *__restrict__ njobs) {
+    __shared__ TriEdge buf[TRI_WARPS][32 * (JOB_U + 1)];
+    const int warp = threadIdx.x >> 5;
+    TriEdge *wb = buf[warp];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * TRI_WARPS;
+    int cnt = 0;
+    const Segment &sg = A.seg0;
+    const int32_t *__restrict__ swl = wl + sg.xbase;  // the segment starts at entry 0
+    TriEdge *sjobs = jobs + sg.xbase / 2;
+    for (int64_t base = wid * (32 * JOB_U); base < sg.g.m; base += nwarps * (32 * JOB_U))
+        tri_jobs_step_ranks<SHARD>(A, sg.g, swl, base, sg.g.m, wb, cnt, sjobs, njobs);
+    tri_jobs_flush(wb, cnt, sjobs, njobs);
 }
 
 // Adds each lane's 8 type-II counters of the warp into cells[40..47] (Tri
@@ -1738,15 +1831,26 @@ void launch_count_segments(const Segment *one, const Segment *d_segs, const int3
         TriEdge *jobs = static_cast<TriEdge *>(sc.jobs);
         const int occ = occupancy(k_tri_join<true, false>);
         const int bps = join_blocks_per_sm > 0 ? std::min(join_blocks_per_sm, occ) : occ;
+        // a whole graph that kept its rank-ordered endpoints: jobs in rank order
+        const bool ranks = one && one->g.sd != nullptr && one->begin == 0 &&
+                           (int64_t)one->end == 2 * one->g.m;
         if (one && own) {
-            TM_LAUNCH((k_tri_jobs<true, true>), (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl, jobs,
-                      njobs);
+            if (ranks)
+                TM_LAUNCH((k_tri_jobs_ranks<true>), (unsigned)stream_blocks, THREADS, 0, s, A,
+                          sc.wl, jobs, njobs);
+            else
+                TM_LAUNCH((k_tri_jobs<true, true>), (unsigned)stream_blocks, THREADS, 0, s, A,
+                          sc.wl, jobs, njobs);
             TM_LAUNCH((k_tri_join<true, true>), (unsigned)(sms * bps), THREADS, 0, s, A, jobs, njobs,
                       tj_pre, heads + 1);
             if (fill) TM_LAUNCH(k_fill_tri_types_seg<true>, 1, 128, 0, s, A);
         } else if (one) {
-            TM_LAUNCH((k_tri_jobs<true, false>), (unsigned)stream_blocks, THREADS, 0, s, A, sc.wl,
-                      jobs, njobs);
+            if (ranks)
+                TM_LAUNCH((k_tri_jobs_ranks<false>), (unsigned)stream_blocks, THREADS, 0, s, A,
+                          sc.wl, jobs, njobs);
+            else
+                TM_LAUNCH((k_tri_jobs<true, false>), (unsigned)stream_blocks, THREADS, 0, s, A,
+                          sc.wl, jobs, njobs);
             TM_LAUNCH((k_tri_join<true, false>), (unsigned)(sms * bps), THREADS, 0, s, A, jobs,
                       njobs, tj_pre, heads + 1);
             if (fill) TM_LAUNCH(k_fill_tri_types_seg<true>, 1, 128, 0, s, A);

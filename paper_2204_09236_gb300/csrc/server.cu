@@ -33,14 +33,14 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 // Device bytes a resident graph holds (the entry arrays tt, tn, tc, cin, lk, off,
-// positions, pair list, hash, Bloom filter) and the extra scratch its build
-// needs at peak.
+// positions, rank-ordered endpoints when kept, pair list, hash, Bloom filter)
+// and the extra scratch its build needs at peak.
 int64_t resident_bytes(int64_t m, int64_t n) {
     int64_t hash = 16;
     while (hash < 2 * m) hash <<= 1;
-    return 64 * m + 4 + 8 * m + 8 * (m + 1) + 16 * hash + 4 * (n + 1) + m + (1 << 20);
+    return 64 * m + 4 + 8 * m + 8 * m + 8 * (m + 1) + 16 * hash + 4 * (n + 1) + m + (1 << 20);
 }
-int64_t build_scratch_bytes(int64_t m) { return 96 * m + (1 << 20); }
+int64_t build_scratch_bytes(int64_t m) { return 104 * m + (1 << 20); }
 
 // Each worker counts its waves in runs of at most count_cap entries with a
 // scratch slab of count_scratch_bytes(count_cap, WAVE_JOBS) bytes that it

@@ -92,6 +92,10 @@ struct DevGraph {
     int32_t *off = nullptr;     // n+1: S_u = entries [off[u], off[u+1])
     int32_t *pos_src = nullptr; // m, by rank: entry of the edge at its source
     int32_t *pos_dst = nullptr; // m, by rank: entry of the edge at its destination
+    // m, by rank: (source << 32) | destination, kept only for a graph whose
+    // entries are concentrated on few nodes (its Tri jobs are then found in
+    // rank order); null otherwise
+    uint64_t *sd = nullptr;
     // pair list, m+1 entries: runs = E_(v,w) (grouped by node pair, ranks
     // ascending); .x = rank of the edge, .y = exclusive prefix over the list of
     // "source is the smaller id" (entry m holds the total).
