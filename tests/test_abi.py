@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every symbol include/tm.h
-declares; its host-only calls (layout, class fold) agree with the oracle.
+declares; its host-only calls (layout, class fold) agree with the oracle, and
+its memory estimate covers a graph's arrays.
 No GPU is needed: nothing here launches a kernel."""
 import ctypes
 import re
@@ -91,3 +92,29 @@ def test_tri_rotation_identity_matches_oracle_classes():
         (i, j, k), = np.argwhere(q[1])
         assert q[0, 1 - k, 1 - j, 1 - i] == 1
         assert q[2, 1 - i, k, j] == 1
+
+
+def test_estimate_covers_the_resident_arrays(lib):
+    """tm_estimate_bytes (host arithmetic, no GPU): a graph's resident estimate
+    covers its arrays in the worst case (every edge its own node pair, the
+    rank-ordered endpoints kept), both figures grow with the graph, and bad
+    sizes are rejected."""
+    for m, n in [(0, 0), (1, 2), (1000, 50), (60_000_000, 2_500_000)]:
+        resident, scratch = lib.tm_estimate_bytes(m, n)
+        slots = 16
+        while slots < 2 * m:
+            slots *= 2
+        arrays = (2 * m * 32          # tt, tn, tc, cin, lk
+                  + 4 * (n + 1)       # off
+                  + 8 * m             # pos_src, pos_dst
+                  + 8 * m             # rank-ordered endpoints
+                  + 8 * (m + 1)       # pair list
+                  + 16 * slots)       # hash at most half full
+        assert resident >= arrays, (m, n)
+        assert scratch >= 104 * m
+    r0, s0 = lib.tm_estimate_bytes(1000, 50)
+    r1, s1 = lib.tm_estimate_bytes(2000, 50)
+    r2, _ = lib.tm_estimate_bytes(2000, 5000)
+    assert r1 > r0 and s1 > s0 and r2 > r1
+    with pytest.raises(lib.TmError):
+        lib.tm_estimate_bytes(-1, 5)
